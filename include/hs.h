@@ -1,0 +1,182 @@
+/*
+ * hs.h - C ABI of the GB300 nested shift-invert MINRES library for the
+ * periodic spin-1/2 random-field Heisenberg chain (Kutsuzawa & Todo,
+ * arXiv:2203.09732).
+ *
+ *   H = sum_{j=1..L} ( S_j . S_{j+1} - h_j Sz_j ),  S_{L+1} = S_1,  J = 1
+ *                                                       (Sec. I, Eq. (1))
+ * in the Sz = 0 sector of even L (dimension n = C(L, L/2)).
+ *
+ * Conventions shared by every call:
+ *   - Basis: site j (1-based) is bit j-1 of a 32-bit word, bit = 1 is spin up.
+ *     The sector states are ranked in ascending integer order; vectors are
+ *     n contiguous elements in that order, on the device unless the argument
+ *     name ends in _host.
+ *   - Ownership: the caller owns every vector argument; the handle owns its
+ *     tables, workspace and CUDA graphs and frees them in hs_free.
+ *   - Streams: all work is enqueued on the stream given to hs_create (NULL =
+ *     legacy default stream). Calls that return host results synchronise that
+ *     stream before returning.
+ *   - Errors: every call returns an hs_status; no call aborts, throws or traps.
+ *     hs_last_error() returns a message for the last failing call on a handle.
+ *     Device-side failures (non-finite values, breakdown) are reported through
+ *     the status, never by a device trap.
+ */
+#ifndef HS_H
+#define HS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hs_handle hs_handle;
+
+typedef enum {
+  HS_OK = 0,
+  HS_BAD_ARG = 1,        /* invalid size, pointer, L, h, sigma or option       */
+  HS_OOM = 2,            /* device or host allocation failed                    */
+  HS_CUDA = 3,           /* a CUDA runtime call failed                          */
+  HS_NOT_CONVERGED = 4,  /* iteration cap reached before the tolerance          */
+  HS_BREAKDOWN = 5,      /* gamma_k = 0 in MINRES, or a Lanczos breakdown       */
+  HS_NONFINITE = 6,      /* NaN/Inf met in a reduction                          */
+  HS_TIMEOUT = 7         /* reserved: bounded device wait expired               */
+} hs_status;
+
+typedef enum { HS_F32 = 0, HS_F64 = 1 } hs_dtype;
+
+/* Diagonal preconditioners M of Sec. II: identity; Jacobi diag|a_ii - sigma|;
+ * row norm r_i = sqrt(|a_ii - sigma|^2 + sum_{k != i} |a_ik|^2). */
+typedef enum { HS_PC_ID = 0, HS_PC_JACOBI = 1, HS_PC_ROWNORM = 2 } hs_precond;
+
+typedef struct {
+  long long iters;     /* total MINRES iterations (all refinement sweeps)        */
+  int sweeps;          /* FP64 refinement sweeps (1 for plain FP64 MINRES)        */
+  int status;          /* hs_status of the solve                                  */
+  double phi;          /* last |phi_k| / beta_1 of the last inner solve           */
+  double resid_minv;   /* final ||b - (H - sigma) x||_{M^-1} / ||b||_{M^-1}, FP64 */
+  double resid_2;      /* final ||b - (H - sigma) x||_2 / ||b||_2, FP64          */
+} hs_minres_info;
+
+typedef struct {
+  int steps;           /* Lanczos steps taken (k at exit)                         */
+  int converged;       /* number of wanted pairs meeting the tolerance           */
+  long long minres_iters; /* MINRES iterations summed over all solves            */
+  int sweeps;          /* refinement sweeps summed over all solves               */
+  double sigma;        /* shift used                                              */
+  double max_resid;    /* max_i ||H psi_i - E_i psi_i||_2 (FP64, certified)       */
+  double seconds_solve;   /* host wall time inside the MINRES solves             */
+  double seconds_total;   /* host wall time of the whole call                    */
+} hs_lanczos_info;
+
+/* Create a handle for chain length L (even, 4 <= L <= 32) and fields
+ * h_host[0..L-1] (h_host[j-1] = h_j of Eq. (1); finite). sigma is the shift of
+ * Algorithm 1; pass NaN to set sigma = (E_min + E_max) / 2 (Sec. IV A), found
+ * by an extremal FP64 Lanczos run on the device. cuda_stream is a
+ * cudaStream_t (may be NULL). Builds the ranking tables on the host and
+ * copies them to the current device. On failure *out is NULL. */
+hs_status hs_create(int L, const double* h_host, double sigma, void* cuda_stream,
+                    hs_handle** out);
+
+/* Free the handle and everything it owns (synchronises its stream first). */
+void hs_free(hs_handle* hd);
+
+/* Message for the last failed call on hd ("" if none; static text if hd NULL). */
+const char* hs_last_error(const hs_handle* hd);
+
+/* n = C(L, L/2). */
+hs_status hs_dim(const hs_handle* hd, long long* n_out);
+
+/* Current sigma; hs_set_sigma replaces it (finite). Cached solver graphs stay
+ * valid: sigma is read from device memory at run time. */
+hs_status hs_get_sigma(const hs_handle* hd, double* sigma_out);
+hs_status hs_set_sigma(hs_handle* hd, double sigma);
+
+/* Extremal eigenvalues by plain FP64 Lanczos on H (three-term recurrence,
+ * T_k re-diagonalised every 10 steps) until both move by < tol; returns
+ * E_min, E_max and (E_min + E_max) / 2 without changing the handle's sigma.
+ * Sec. IV A defines sigma from these. */
+hs_status hs_extremal(hs_handle* hd, int max_steps, double tol, double* emin_out,
+                      double* emax_out, double* mid_out);
+
+/* Ranking of the Sz = 0 sector (row a1): states_dev[t] = the state of rank
+ * first + t, t < count (bit-exact, ascending integer order). */
+hs_status hs_unrank(hs_handle* hd, long long first, long long count,
+                    unsigned int* states_dev);
+/* ranks_dev[t] = rank of states_dev[t], or -1 if the word is not an L-bit word
+ * of popcount L/2. */
+hs_status hs_rank(hs_handle* hd, const unsigned int* states_dev, long long count,
+                  long long* ranks_dev);
+
+/* diag_dev[i] = a_ii (diagonal of H, FP64, may be NULL); minv_dev[i] = 1 / M_ii
+ * of preconditioner pc at the current sigma (FP64, may be NULL). Sec. II. */
+hs_status hs_diag(hs_handle* hd, double* diag_dev, hs_precond pc, double* minv_dev);
+
+/* Matrix-free y = H x (shifted = 0) or y = (H - sigma) x (shifted = 1), in
+ * FP32 (x, y float, FP32 accumulation) or FP64. x and y must not overlap.
+ * Eq. (1); element (i, k) for i != k is 1/2 exactly when states i and k differ
+ * by the flip of one antiparallel bond (Appendix C). */
+hs_status hs_matvec(hs_handle* hd, const void* x_dev, void* y_dev, hs_dtype dtype,
+                    int shifted);
+
+/* Solve (H - sigma) x = b by the preconditioned MINRES of Algorithm 2
+ * (Appendix A), x0 = 0, stopping when |phi_k| <= tol * beta_1 or after kmax
+ * iterations (kmax <= 0: 20 n).
+ *   mixed = 0: plain FP64 MINRES.
+ *   mixed = 1: FP32 MINRES (FP32 vectors and H x, FP64 scalar recurrences)
+ *              inside FP64 iterative refinement of the residual
+ *              r = b - (H - sigma) x, until ||r||_{M^-1} <= tol ||b||_{M^-1}
+ *              (each sweep runs to the relative tolerance inner_tol).
+ * b_dev and x_dev are FP64, n elements, may not overlap. info may be NULL.
+ * Returns HS_NOT_CONVERGED (x still holds the last iterate) if the cap is hit. */
+hs_status hs_minres(hs_handle* hd, const double* b_dev, double* x_dev, double tol,
+                    long long kmax, hs_precond pc, int mixed, double inner_tol,
+                    hs_minres_info* info);
+
+/* One FP32 MINRES solve without refinement (Algorithm 2 in FP32 vectors,
+ * FP64 scalars): b_dev, x_dev float. For tests of the FP32 inner solver. */
+hs_status hs_minres_f32(hs_handle* hd, const float* b_dev, float* x_dev, double tol,
+                        long long kmax, hs_precond pc, hs_minres_info* info);
+
+/* The K eigenpairs of H nearest sigma by the nested shift-invert Lanczos of
+ * Algorithm 1 with full reorthogonalisation (two classical Gram-Schmidt
+ * passes) and MINRES inside every step.
+ *   K >= 1; m_max: Lanczos step cap (<= 0: max(130, 3K + 30)); tol: stop when
+ *   every wanted Ritz pair has beta_{k+1} |y_{k,i}| <= tol |theta_i|;
+ *   seed: SplitMix64 stream of the start vector (entries uniform on [-1, 1));
+ *   v0_dev: optional FP64 start vector (overrides seed); mixed, pc, inner_tol:
+ *   as hs_minres, with MINRES tolerance minres_tol.
+ * Outputs: evals_host[K] ordered by |E - sigma| (ties by E), E_i the Rayleigh
+ * quotient of psi_i; evecs_dev (K x n FP64, vector i at evecs_dev + i n; may be
+ * NULL); resid_host[K] = ||H psi_i - E_i psi_i||_2 (may be NULL).
+ * Workspace: m_max + 8 FP64 vectors plus the MINRES vectors. */
+hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol,
+                          unsigned long long seed, const double* v0_dev, int mixed,
+                          hs_precond pc, double minres_tol, double inner_tol,
+                          double* evals_host, double* evecs_dev, double* resid_host,
+                          hs_lanczos_info* info);
+
+/* End-to-end convenience call with host buffers only: creates a handle on the
+ * current device, runs hs_lanczos_eigs, copies the eigenvectors to
+ * evecs_host (K x n, may be NULL) and frees everything. sigma NaN = midpoint. */
+hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_max,
+                       double tol, unsigned long long seed, int mixed, hs_precond pc,
+                       double minres_tol, double inner_tol, double* evals_host,
+                       double* evecs_host, double* resid_host, double* z_host,
+                       hs_lanczos_info* info);
+
+/* Twist overlap z_i = <psi_i| U_twist |psi_i>, U_twist = exp[i 2pi/L sum_j j Sz_j]
+ * (Sec. III), for K real FP64 vectors psi_dev + i n (not normalised by the
+ * call). z_host[2 i] = Re z_i, z_host[2 i + 1] = Im z_i. */
+hs_status hs_twist(hs_handle* hd, const double* psi_dev, int K, double* z_host);
+
+/* Host-only: eigen-decomposition of the symmetric tridiagonal T (diagonal
+ * alpha[0..k), off-diagonal beta[0..k-1)) by implicit QL with Wilkinson shifts.
+ * theta[k] ascending; Y (k x k, column-major, may be NULL) eigenvectors.
+ * Used for T_k of Algorithm 1. No GPU needed. */
+hs_status hs_tridiag_eig(int k, const double* alpha, const double* beta, double* theta,
+                         double* Y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HS_H */

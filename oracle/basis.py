@@ -42,3 +42,38 @@ def spins(states, L):
     """Sz_j of each state as an (n, L) float array of +-1/2, column j-1 = site j."""
     bits = (states[:, None] >> np.arange(L)[None, :]) & 1
     return np.where(bits == 1, 0.5, -0.5)
+
+
+def _binom(n, r):
+    from math import comb
+    return comb(n, r) if 0 <= r <= n else 0
+
+
+def rank_count(s, L):
+    """Rank of one state word by counting the sector words below it: for every
+    set bit p (scanned from the top), the words that agree above p and have 0
+    at p number C(p, remaining ones). No table; used for large L."""
+    s = int(s)
+    ones = L // 2
+    r = 0
+    for p in range(L - 1, -1, -1):
+        if (s >> p) & 1:
+            r += _binom(p, ones)
+            ones -= 1
+    return r
+
+
+def unrank_count(r, L):
+    """Inverse of rank_count: the state word of rank r."""
+    r = int(r)
+    ones = L // 2
+    s = 0
+    for p in range(L - 1, -1, -1):
+        if ones == 0:
+            break
+        c = _binom(p, ones)
+        if r >= c:
+            s |= 1 << p
+            r -= c
+            ones -= 1
+    return s

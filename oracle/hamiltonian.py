@@ -81,3 +81,28 @@ def precond_diag(H, diag, sigma, kind):
 def matvec(H, x, sigma=0.0):
     """(H - sigma) x with the explicit matrix."""
     return H @ x - sigma * x
+
+
+def row(L, h, s, sigma=0.0):
+    """Row of (H - sigma) for one state word s, from Eq. (1) directly:
+    returns (diagonal a_ss - sigma, [(rank of flipped state, 1/2), ...]).
+    Ranks come from basis.rank_count (no enumeration), for sampled rows at
+    large L."""
+    d = 0.0
+    off = []
+    for (a, b) in bonds(L):
+        ba, bb = (s >> a) & 1, (s >> b) & 1
+        if ba == bb:
+            d += 0.25
+        else:
+            d -= 0.25
+            off.append((basis.rank_count(s ^ ((1 << a) | (1 << b)), L), 0.5))
+    for j in range(L):
+        d -= h[j] * (0.5 if (s >> j) & 1 else -0.5)
+    return d - sigma, off
+
+
+def rownorm(L, h, s, sigma):
+    """Row-norm preconditioner entry r_i of Sec. II for one state."""
+    d, off = row(L, h, s, sigma)
+    return np.sqrt(d * d + sum(v * v for _, v in off))

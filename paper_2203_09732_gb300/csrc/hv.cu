@@ -1,0 +1,224 @@
+// Matrix-free H x (Eq. (1)), the basis ranking (Sec. I: Sz = 0 sector in
+// ascending integer order), the diagonal / preconditioner export (Sec. II) and
+// the FP64 refinement residual r = b - (H - sigma) x.
+#include "rows.cuh"
+
+namespace hs {
+
+// ---------------------------------------------------------------------------
+// y = (H - sigma * shifted) x. Persistent CTAs walk the tiles in rank order.
+template <typename T>
+__global__ void __launch_bounds__(HV_THREADS) k_matvec(Geo g, const T* __restrict__ x,
+                                                       T* __restrict__ y, const double* d_sigma,
+                                                       int shifted) {
+  extern __shared__ __align__(16) char smem[];
+  RowSmem s = row_smem_carve(smem, g);
+  constexpr bool is64 = sizeof(T) == 8;
+  row_smem_fill(s, g, is64);
+  const double sigma = shifted ? *d_sigma : 0.0;
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const Tile tl = g.tiles[t];
+    __syncthreads();
+    tile_load(s, g, tl, sigma);
+    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
+      const LowEntry e = s.low[li];
+      const uint32_t xc = cut_mask(e, b);
+      T xi;
+      const T off = offdiag_row<T>(x, s, b, e, (uint32_t)r, xc, xi);
+      T a;
+      if constexpr (is64) a = diag_d(s.dlow64[li], b, xc);
+      else a = diag_f(e, b, xc);
+      y[b.R + r] = a * xi + off;
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Ranking: colex rank of the popcount-N word s = sum_i C(p_i, i) over its set
+// bits p_1 < p_2 < ... (equal to the ascending-integer rank of the sector).
+__global__ void k_unrank(const uint32_t* __restrict__ binom, int L, int N, long long first,
+                         long long count, unsigned int* __restrict__ out) {
+  const int W = LMAX / 2 + 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x) {
+    uint32_t r = (uint32_t)(first + t);
+    uint32_t s = 0;
+    int p = L - 1;
+    for (int c = N; c >= 1; --c) {
+      while (binom[p * W + c] > r) --p;
+      s |= 1u << p;
+      r -= binom[p * W + c];
+      --p;
+    }
+    out[t] = s;
+  }
+}
+
+__global__ void k_rank(const uint32_t* __restrict__ binom, int L, int N,
+                       const unsigned int* __restrict__ st, long long count,
+                       long long* __restrict__ out) {
+  const int W = LMAX / 2 + 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x) {
+    uint32_t s = st[t];
+    if ((L < 32 && (s >> L) != 0u) || __popc(s) != N) { out[t] = -1; continue; }
+    long long r = 0;
+    int c = 1;
+    while (s) {
+      const int p = __ffs(s) - 1;
+      r += binom[p * W + c];
+      ++c;
+      s &= s - 1u;
+    }
+    out[t] = r;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// diag[i] = a_ii, minv[i] = 1 / M_ii (FP64).
+__global__ void __launch_bounds__(HV_THREADS) k_diag(Geo g, double* diag, double* minv, int pc,
+                                                     const double* d_sigma) {
+  extern __shared__ __align__(16) char smem[];
+  RowSmem s = row_smem_carve(smem, g);
+  row_smem_fill(s, g, true);
+  const double sigma = *d_sigma;
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const Tile tl = g.tiles[t];
+    __syncthreads();
+    tile_load(s, g, tl, sigma);
+    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
+      const LowEntry e = s.low[li];
+      const uint32_t xc = cut_mask(e, b);
+      const double am = diag_d(s.dlow64[li], b, xc);
+      const uint32_t i = b.R + r;
+      if (diag) diag[i] = am + sigma;
+      if (minv) {
+        const int naf = naf_row(e, b, xc);
+        double m = pc == 0 ? 1.0 : (pc == 1 ? fabs(am) : sqrt(am * am + 0.25 * naf));
+        minv[i] = 1.0 / m;
+      }
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual r = b - (H - sigma) x with per-CTA partial sums
+// [sum r^2 / M, sum r^2, sum b^2 / M, sum b^2] (host adds them in order).
+template <int PC>
+__global__ void __launch_bounds__(HV_THREADS) k_resid64(Geo g, const double* __restrict__ bv,
+                                                        const double* __restrict__ x,
+                                                        double* __restrict__ rv,
+                                                        const double* d_sigma,
+                                                        double* partial) {
+  extern __shared__ __align__(16) char smem[];
+  RowSmem s = row_smem_carve(smem, g);
+  row_smem_fill(s, g, true);
+  const double sigma = *d_sigma;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
+    const Tile tl = g.tiles[t];
+    __syncthreads();
+    tile_load(s, g, tl, sigma);
+    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
+      const LowEntry e = s.low[li];
+      const uint32_t xc = cut_mask(e, b);
+      double xi;
+      const double off = offdiag_row<double>(x, s, b, e, (uint32_t)r, xc, xi);
+      const double am = diag_d(s.dlow64[li], b, xc);
+      const uint32_t i = b.R + r;
+      const double bi = bv[i];
+      const double ri = bi - (am * xi + off);
+      rv[i] = ri;
+      const double m = precond_d<PC>(am, naf_row(e, b, xc));
+      acc[0] += ri * ri / m;
+      acc[1] += ri * ri;
+      acc[2] += bi * bi / m;
+      acc[3] += bi * bi;
+    });
+  }
+  block_sum<4>(acc, s.red);
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 4; ++j) partial[blockIdx.x * 4 + j] = acc[j];
+}
+
+// ---------------------------------------------------------------------------
+static size_t smem_of(const hs_handle* hd) {
+  return row_smem_bytes((int)hd->low.size(), (int)hd->nb.size());
+}
+
+template <typename K>
+static hs_status prep_smem(hs_handle* hd, K kern, size_t bytes) {
+  if (bytes > 48 * 1024)
+    HS_CUDA_TRY(hd, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes));
+  return HS_OK;
+}
+
+hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted) {
+  const Geo g = hd->geo();
+  const size_t sm = smem_of(hd);
+  const int grid = row_grid(hd);
+  if (dt == HS_F32) {
+    if (prep_smem(hd, k_matvec<float>, sm) != HS_OK) return HS_CUDA;
+    k_matvec<float><<<grid, HV_THREADS, sm, hd->stream>>>(
+        g, static_cast<const float*>(x), static_cast<float*>(y), hd->d_sigma, shifted);
+  } else {
+    if (prep_smem(hd, k_matvec<double>, sm) != HS_OK) return HS_CUDA;
+    k_matvec<double><<<grid, HV_THREADS, sm, hd->stream>>>(
+        g, static_cast<const double*>(x), static_cast<double*>(y), hd->d_sigma, shifted);
+  }
+  HS_CUDA_TRY(hd, cudaGetLastError());
+  return HS_OK;
+}
+
+hs_status launch_unrank(hs_handle* hd, long long first, long long count, unsigned int* out) {
+  if (count <= 0) return HS_OK;
+  const int grid = (int)std::min<long long>((count + 255) / 256, hd->num_sms * 8LL);
+  k_unrank<<<grid, 256, 0, hd->stream>>>(hd->d_binom, hd->L, hd->N, first, count, out);
+  HS_CUDA_TRY(hd, cudaGetLastError());
+  return HS_OK;
+}
+
+hs_status launch_rank(hs_handle* hd, const unsigned int* st, long long count, long long* out) {
+  if (count <= 0) return HS_OK;
+  const int grid = (int)std::min<long long>((count + 255) / 256, hd->num_sms * 8LL);
+  k_rank<<<grid, 256, 0, hd->stream>>>(hd->d_binom, hd->L, hd->N, st, count, out);
+  HS_CUDA_TRY(hd, cudaGetLastError());
+  return HS_OK;
+}
+
+hs_status launch_diag(hs_handle* hd, double* diag, hs_precond pc, double* minv) {
+  const size_t sm = smem_of(hd);
+  if (prep_smem(hd, k_diag, sm) != HS_OK) return HS_CUDA;
+  k_diag<<<row_grid(hd), HV_THREADS, sm, hd->stream>>>(hd->geo(), diag, minv, (int)pc,
+                                                       hd->d_sigma);
+  HS_CUDA_TRY(hd, cudaGetLastError());
+  return HS_OK;
+}
+
+hs_status resid64(hs_handle* hd, const double* b, const double* x, double* r, hs_precond pc,
+                  double sums_out[4]) {
+  hs_status st = ensure_reduce(hd);
+  if (st != HS_OK) return st;
+  const size_t sm = smem_of(hd);
+  const int grid = row_grid(hd);
+  const Geo g = hd->geo();
+  switch (pc) {
+    case HS_PC_ID:
+      if (prep_smem(hd, k_resid64<0>, sm) != HS_OK) return HS_CUDA;
+      k_resid64<0><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial);
+      break;
+    case HS_PC_JACOBI:
+      if (prep_smem(hd, k_resid64<1>, sm) != HS_OK) return HS_CUDA;
+      k_resid64<1><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial);
+      break;
+    default:
+      if (prep_smem(hd, k_resid64<2>, sm) != HS_OK) return HS_CUDA;
+      k_resid64<2><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial);
+      break;
+  }
+  HS_CUDA_TRY(hd, cudaGetLastError());
+  return sum_partials(hd, grid, 4, sums_out);
+}
+
+}  // namespace hs

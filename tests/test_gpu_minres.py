@@ -1,0 +1,179 @@
+"""GPU parity of rows a4-a5: the preconditioned MINRES of Algorithm 2 (FP64
+and FP32) and the FP64 iterative refinement, against the CPU oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import hamiltonian, minres
+from paper_2203_09732_gb300 import inputs
+from tests.gpu_util import need_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _sys(L, h=3.0, seed=0, sigma=0.1234):
+    hv = inputs.disorder(L, h, seed)
+    H, diag, st = hamiltonian.build(L, hv)
+    A = (H - sigma * sp.identity(H.shape[0])).tocsr()
+    return hv, H, diag, A, sigma
+
+
+@pytest.mark.parametrize("L", [6, 8, 10, 12])
+@pytest.mark.parametrize("kind", ["id", "jacobi", "row"])
+@pytest.mark.parametrize("k", [1, 2, 3, 7, 20])
+def test_iterates_match_oracle_fp64(L, kind, k):
+    """x_k after k iterations of Algorithm 2 (FP64): same algorithm, so the
+    iterates agree up to the rounding of the reductions."""
+    hs = need_gpu()
+    hv, H, diag, A, sigma = _sys(L)
+    b = inputs.gaussian(A.shape[0], 11)
+    M = hamiltonian.precond_diag(H, diag, sigma, kind)
+    xr, kr, phir = minres.pminres(A, b, 1.0 / M, kmax=k, tol=0.0)
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        x, info = c.minres(to_dev(b), tol=0.0, kmax=k, precond=kind, allow_not_converged=True)
+    assert info["iters"] == k
+    x = x.cpu().numpy()
+    # the reductions round in a different order; the recurrence amplifies
+    # that by the spread of the preconditioner and, as the Lanczos vectors
+    # lose orthogonality, with k (k reaches n = 20 at L = 6)
+    spread = M.max() / M.min()
+    tol = (1e-12 if k <= 7 else 1e-8) * spread
+    assert np.linalg.norm(x - xr) <= tol * np.linalg.norm(xr)
+    assert abs(info["phi"] - abs(phir) / np.sqrt(b @ (b / M))) <= tol
+
+
+@pytest.mark.parametrize("L", [8, 12, 14])
+@pytest.mark.parametrize("kind", ["id", "row"])
+def test_solve_fp64(L, kind):
+    hs = need_gpu()
+    hv, H, diag, A, sigma = _sys(L, seed=L)
+    b = inputs.gaussian(A.shape[0], 3)
+    xr = sp.linalg.spsolve(A.tocsc(), b)
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        x, info = c.minres(to_dev(b), tol=1e-12, precond=kind)
+    assert info["status"] == 0
+    x = x.cpu().numpy()
+    assert np.linalg.norm(A @ x - b) <= 1e-9 * np.linalg.norm(b)
+    cond_err = np.linalg.norm(x - xr) / np.linalg.norm(xr)
+    assert cond_err < 1e-6
+
+
+@pytest.mark.parametrize("L", [10, 14])
+def test_fp32_solver(L):
+    hs = need_gpu()
+    hv, H, diag, A, sigma = _sys(L, seed=2)
+    b = inputs.gaussian(A.shape[0], 4).astype(np.float32)
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        x, info = c.minres_f32(to_dev(b), tol=1e-4, precond="row", allow_not_converged=True)
+    x = x.cpu().double().numpy()
+    rel = np.linalg.norm(A @ x - b) / np.linalg.norm(b)
+    assert rel < 1e-2, rel
+    assert info["iters"] > 0
+
+
+@pytest.mark.parametrize("L", [10, 14, 16])
+def test_mixed_refinement_reaches_fp64(L):
+    hs = need_gpu()
+    hv, H, diag, A, sigma = _sys(L, seed=5)
+    b = inputs.gaussian(A.shape[0], 6)
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        x, info = c.minres(to_dev(b), tol=1e-12, precond="row", mixed=True, inner_tol=1e-4)
+        x64, info64 = c.minres(to_dev(b), tol=1e-12, precond="row", mixed=False)
+    x = x.cpu().numpy()
+    M = hamiltonian.precond_diag(H, diag, sigma, "row")
+    r = b - A @ x
+    assert np.sqrt(r @ (r / M)) <= 1.0001e-12 * np.sqrt(b @ (b / M))
+    assert info["sweeps"] >= 2 and info["resid_minv"] <= 1e-12
+    assert np.linalg.norm(x - x64.cpu().numpy()) <= 1e-7 * np.linalg.norm(x)
+
+
+def test_edge_cases():
+    hs = need_gpu()
+    L = 8
+    hv, H, diag, A, sigma = _sys(L)
+    n = A.shape[0]
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        # zero right-hand side: beta_1 = 0, x = 0, no iterations
+        x, info = c.minres(torch.zeros(n, dtype=torch.float64, device="cuda"))
+        assert info["iters"] == 0 and not x.abs().max().item()
+        # kmax = 1 stops early with HS_NOT_CONVERGED
+        with pytest.raises(hs.HSError) as e:
+            c.minres(to_dev(inputs.gaussian(n, 1)), kmax=1)
+        assert e.value.status == hs.HS_NOT_CONVERGED
+        # NaN in b
+        bn = inputs.gaussian(n, 2)
+        bn[3] = np.nan
+        with pytest.raises(hs.HSError) as e:
+            c.minres(to_dev(bn))
+        assert e.value.status == hs.HS_NONFINITE
+        # Jacobi with a_ii == sigma (Sec. II assumes a_ii != sigma)
+        c.sigma = float(diag[5])
+        with pytest.raises(hs.HSError) as e:
+            c.minres(to_dev(inputs.gaussian(n, 1)), precond="jacobi")
+        assert e.value.status == hs.HS_BAD_ARG
+
+
+def test_smallest_chain_exact():
+    """L = 4 (n = 6): MINRES is exact within n steps."""
+    hs = need_gpu()
+    hv, H, diag, A, sigma = _sys(4, seed=1, sigma=0.3)
+    b = inputs.gaussian(6, 9)
+    with hs.Chain(4, hv, sigma=sigma) as c:
+        x, info = c.minres(to_dev(b), tol=1e-14)
+    assert np.linalg.norm(A @ x.cpu().numpy() - b) < 1e-12
+    assert info["iters"] <= 6
+
+
+def test_barrier_timeout_reports_status(monkeypatch):
+    """The persistent solver's grid barrier gives up after its poll limit and
+    returns HS_TIMEOUT; the context stays usable (no trap, no fault)."""
+    hs = need_gpu()
+    L = 16
+    hv, H, diag, A, sigma = _sys(L, seed=3)
+    b = to_dev(inputs.gaussian(A.shape[0], 1))
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        monkeypatch.setenv("HS_BARRIER_LIMIT", "0")
+        with pytest.raises(hs.HSError) as e:
+            c.minres(b, tol=1e-8)
+        assert e.value.status == hs.HS_TIMEOUT
+        monkeypatch.delenv("HS_BARRIER_LIMIT")
+        x, info = c.minres(b, tol=1e-8)
+        assert info["status"] == 0
+    assert np.linalg.norm(A @ x.cpu().numpy() - b.cpu().numpy()) < 1e-6 * np.linalg.norm(b.cpu().numpy())
+
+
+@pytest.mark.parametrize("L", [12, 16])
+def test_graph_path_matches_persistent(L, monkeypatch):
+    """The per-pass (graph) fallback and the persistent kernel run the same
+    row passes: identical iteration counts, iterates equal to rounding."""
+    hs = need_gpu()
+    hv, H, diag, A, sigma = _sys(L, seed=7)
+    b = to_dev(inputs.gaussian(A.shape[0], 2))
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        x1, i1 = c.minres(b, tol=1e-10)
+    monkeypatch.setenv("HS_MINRES_GRAPH", "1")
+    import subprocess, sys, os
+    code = f"""
+import sys; sys.path.insert(0, {os.getcwd()!r})
+import numpy as np, torch
+from paper_2203_09732_gb300 import hs, inputs
+hv = inputs.disorder({L}, 3.0, 7)
+with hs.Chain({L}, hv, sigma={sigma!r}) as c:
+    b = torch.from_numpy(inputs.gaussian(c.n, 2)).cuda()
+    x, i = c.minres(b, tol=1e-10)
+    np.save(sys.argv[1], x.cpu().numpy()); print(i['iters'])
+"""
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        f = os.path.join(d, "x.npy")
+        r = subprocess.run([sys.executable, "-c", code, f], capture_output=True, text=True,
+                           env=dict(os.environ, HS_MINRES_GRAPH="1"))
+        assert r.returncode == 0, r.stderr
+        it2 = int(r.stdout.split()[-1])
+        x2 = np.load(f)
+    # same passes, different reduction order: after ~n iterations the counts
+    # drift by rounding; both solutions meet the tolerance
+    assert abs(it2 - i1["iters"]) <= 0.02 * i1["iters"] + 5
+    bb = b.cpu().numpy()
+    for x in (x2, x1.cpu().numpy()):
+        assert np.linalg.norm(A @ x - bb) <= 1e-7 * np.linalg.norm(bb)

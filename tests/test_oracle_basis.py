@@ -30,3 +30,11 @@ def test_chunked_enumeration_matches():
     a = basis.enumerate_states(14)
     b = basis.enumerate_states(14, chunk=1000)
     assert (a == b).all()
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10, 12])
+def test_counting_rank_matches_enumeration(L):
+    st = basis.enumerate_states(L)
+    for i in range(0, len(st), max(1, len(st) // 97)):
+        assert basis.rank_count(st[i], L) == i
+        assert basis.unrank_count(i, L) == st[i]

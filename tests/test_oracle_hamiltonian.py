@@ -140,3 +140,21 @@ def test_preconditioners():
     assert (hamiltonian.precond_diag(H, diag, sigma, "id") == 1).all()
     with pytest.raises(ValueError):
         hamiltonian.precond_diag(H, diag, diag[5], "jacobi")
+
+
+@pytest.mark.parametrize("L", [6, 10])
+def test_row_matches_explicit_matrix(L):
+    h = inputs.disorder(L, 2.5, 4)
+    H, diag, st = hamiltonian.build(L, h)
+    D = H.toarray()
+    sigma = 0.7
+    for i in range(0, len(st), 7):
+        d, off = hamiltonian.row(L, h, int(st[i]), sigma)
+        ref = D[i].copy()
+        ref[i] -= sigma
+        mine = np.zeros(len(st))
+        mine[i] = d
+        for j, v in off:
+            mine[j] += v
+        assert np.abs(mine - ref).max() < 1e-13
+        assert abs(hamiltonian.rownorm(L, h, int(st[i]), sigma) - np.linalg.norm(ref)) < 1e-12
