@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Benchmark of the nested shift-invert MINRES eigensolver (Kutsuzawa & Todo,
+arXiv:2203.09732) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one disorder realisation of the L = 20 workload (dimension 184756,
+h_j ~ U[-h, h] with h cycling over {1, 2, 3, 4, 5} and seeds 0..4, sigma at the
+spectrum midpoint, 20 eigenpairs nearest sigma) solved end to end on the GPU by
+shift-invert Lanczos with FP32 MINRES inside FP64 iterative refinement. The
+printed value is eigenpairs per second over the timed steps. A full solve at
+L = 28 needs about n = 4e7 MINRES iterations per Lanczos step (hours), so the
+L = 28 part of the metric is the H x bandwidth, reported in `roofline`.
+
+Several GPUs (torchrun): independent realisations per rank, no collective on
+the data path (replicas); value = all eigenpairs / max rank time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigenpairs/s near sigma at L=28 (FP32+refine vs FP64); H*v GB/s vs HBM peak"
+UNIT = "eigenpairs/s"
+HS_VALUES = (1.0, 2.0, 3.0, 4.0, 5.0)
+SEEDS = (0, 1, 2, 3, 4)
+FALLBACK_HBM_GBS = 6800.0
+# Lanczos steps per wanted eigenpair in the paper: m = 130 for 50 eigenpairs (Sec. IV A).
+PAPER_M_PER_PAIR = 130.0 / 50.0
+
+
+def realisation(idx, L):
+    from paper_2203_09732_gb300 import inputs
+    h = HS_VALUES[idx % len(HS_VALUES)]
+    seed = SEEDS[(idx // len(HS_VALUES)) % len(SEEDS)]
+    return h, seed, inputs.disorder(L, h, seed)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--L", type=int, default=20)
+    ap.add_argument("--K", type=int, default=20)
+    ap.add_argument("--hv-L", type=int, default=28, dest="hv_L")
+    ap.add_argument("--minres-tol", type=float, default=1e-10, dest="minres_tol")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback (profiling recipe 6.8 TB/s)"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("rows.cuh", "hv.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2203_09732_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name):
+    """dram bytes per launch recorded in profiles/<name>.md, if the kernel
+    sources still match the hash stored there."""
+    p = os.path.join(ROOT, "profiles", name + ".md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def hv_roofline(torch, hs, L, stream):
+    """H x at L in FP32 (the kernel of the MINRES hot loop), timed with CUDA
+    events on the launching stream; inputs (2 x 160 MB at L = 28) exceed L2."""
+    from paper_2203_09732_gb300 import inputs
+    out = {}
+    with hs.Chain(L, inputs.disorder(L, 3.7, 0), sigma=0.0, stream=stream) as c:
+        n = c.n
+        for name, dt, w in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+            x = torch.randn(n, dtype=dt, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(3):
+                c.matvec(x, y, shifted=True)
+            torch.cuda.synchronize()
+            reps = 20 if name == "f32" else 5
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                c.matvec(x, y, shifted=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3 / reps
+            out[name] = {"n": n, "seconds": sec, "bytes": 2 * n * w}
+            del x, y
+    return out
+
+
+def oracle_sample(L, h, seconds=10.0):
+    """Oracle (CPU, FP64) seconds per MINRES iteration of Algorithm 2 at L,
+    from a bounded run of about `seconds`."""
+    import scipy.sparse as sp
+
+    from oracle import hamiltonian, minres
+    from paper_2203_09732_gb300 import inputs
+    H, diag, st = hamiltonian.build(L, h)
+    sigma = 0.0
+    A = (H - sigma * sp.identity(H.shape[0])).tocsr()
+    Minv = 1.0 / hamiltonian.precond_diag(H, diag, sigma, "row")
+    b = inputs.gaussian(H.shape[0], 1)
+    it = 50
+    minres.pminres(A, b, Minv, kmax=5, tol=0.0)
+    while True:
+        t0 = time.perf_counter()
+        minres.pminres(A, b, Minv, kmax=it, tol=0.0)
+        dt = time.perf_counter() - t0
+        if dt > seconds / 4 or it >= 100000:
+            break
+        it *= 4
+    return dt / it, it, dt
+
+
+def oracle_iters_per_n(Ls=14):
+    """MINRES iterations per unit dimension for a full FP64 solve (row-norm
+    preconditioner, relative tolerance 1e-10), measured by the oracle at a
+    small L (time grows as n^2, Sec. IV A: iterations grow as n)."""
+    import scipy.sparse as sp
+
+    from oracle import hamiltonian, lanczos, minres
+    from paper_2203_09732_gb300 import inputs
+    h = inputs.disorder(Ls, 3.0, 0)
+    H, diag, st = hamiltonian.build(Ls, h)
+    sigma = lanczos.sigma_midpoint(H)
+    A = (H - sigma * sp.identity(H.shape[0])).tocsr()
+    Minv = 1.0 / hamiltonian.precond_diag(H, diag, sigma, "row")
+    b = inputs.gaussian(H.shape[0], 1)
+    x, k, phi = minres.pminres(A, b, Minv, tol=1e-10, kmax=50 * H.shape[0])
+    return k / H.shape[0]
+
+
+def cpu_baseline(L, K, sample_s=10.0):
+    """The oracle as it stands, on a bounded sample, scaled to eigenpairs/s:
+    K / (m x iterations-per-solve x seconds-per-iteration), with m = 2.6 K
+    Lanczos steps (the paper's 130 steps for 50 pairs) and iterations per
+    solve = c n, c from a full oracle solve at L = 14."""
+    from paper_2203_09732_gb300 import inputs
+    h = realisation(0, L)[2]
+    t0 = time.perf_counter()
+    t_it, its, dt = oracle_sample(L, h, sample_s)
+    c = oracle_iters_per_n()
+    n = inputs.dim(L)
+    m = PAPER_M_PER_PAIR * K
+    total = m * c * n * t_it
+    wall = time.perf_counter() - t0
+    return {
+        "value": K / total, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+        "sample": (f"oracle Algorithm 2 at L={L} for {its} iterations ({dt:.1f} s, "
+                   f"{t_it * 1e3:.2f} ms/iteration, scipy CSR FP64), scaled by m={m:.0f} Lanczos "
+                   f"steps x {c:.2f} n iterations per solve (c from a full oracle solve at L=14)"),
+        "sample_wall_s": wall,
+    }
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed on this host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    L, K = args.L, args.K
+    for _ in range(args.warmup):
+        oracle_sample(L, realisation(0, L)[2], 2.0)
+    t0 = time.perf_counter()
+    vals = []
+    for s in range(args.steps):
+        cb = cpu_baseline(L, K, sample_s=8.0)
+        vals.append(cb["value"])
+    wall = time.perf_counter() - t0
+    v = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded disorder realisations)",
+        "config": {"workload": f"L={L} random-field Heisenberg chain, Sz=0 (dim {realisation_dim(L)}), "
+                               f"{K} eigenpairs nearest the spectrum midpoint, h in {{1..5}} x seeds 0..4",
+                   "L": L, "K": K},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": cb["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def realisation_dim(L):
+    from math import comb
+    return comb(L, L // 2)
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2203_09732_gb300 import hs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    hs.load()
+    stream = torch.cuda.current_stream()
+    L, K = args.L, args.K
+    n = realisation_dim(L)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(idx, record=None):
+        h, seed, hv = realisation(idx, L)
+        with hs.Chain(L, hv, stream=stream) as c:   # sigma = midpoint (extremal Lanczos)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ev, vecs, res, info = c.eigs(K, mixed=True, minres_tol=args.minres_tol, seed=idx,
+                                         allow_not_converged=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            z = c.twist(vecs)
+        if record is not None:
+            record.append({"h": h, "seed": seed, "seconds": sec, "info": info,
+                           "max_resid": float(res.max()), "zabs2_mean": float(np.mean(np.abs(z) ** 2))})
+        return sec
+
+    # warm-up steps (untimed): realisations disjoint from the timed ones
+    for w in range(args.warmup):
+        step(1000 + rank + world * w)
+    recs = []
+    launches0 = hs.kernel_launches()
+    barrier()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        dev_sec = 0.0
+        for s in range(args.steps):
+            dev_sec += step(rank + world * s, recs)
+        barrier()
+        wall = time.perf_counter() - t0
+    launches = hs.kernel_launches() - launches0
+    tmax = dev_sec
+    if dist is not None:
+        t = torch.tensor([dev_sec], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    total_pairs = K * args.steps * world
+    value = total_pairs / tmax
+
+    # end to end through the C ABI with host buffers (hs_eigs_host)
+    e2e_steps = max(1, min(2, args.steps))
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        h, seed, hv = realisation(rank + world * s, L)
+        hs.eigs_host(L, hv, K, mixed=True, minres_tol=args.minres_tol, seed=s)
+    barrier()
+    e2e_sec = time.perf_counter() - t0
+    e2e_val = K * e2e_steps * world / e2e_sec
+    k_lo = 10 if L >= 22 else 8
+    nblocks = sum(1 for H in range(1 << (L - k_lo)) if 0 <= L // 2 - bin(H).count("1") <= k_lo)
+    h2d = 8 * L + 32 * (1 << k_lo) + 128 * nblocks + 8 * 33 * 18
+    d2h = K * n * 8 + K * 8 + K * 8 + 2 * K * 8
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    extra = {}
+    # FP32+refinement vs plain FP64, one solve each on the first timed realisation
+    if not args.no_fp64:
+        h, seed, hv = realisation(0, L)
+        with hs.Chain(L, hv, stream=stream) as c:
+            b = torch.randn(c.n, dtype=torch.float64, device="cuda")
+            res = {}
+            for mode in ("fp32_ir", "fp64"):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                x, info = c.minres(b, tol=args.minres_tol, mixed=(mode == "fp32_ir"),
+                                   allow_not_converged=True)
+                torch.cuda.synchronize()
+                res[mode] = {"seconds": time.perf_counter() - t0, "iters": info["iters"],
+                             "sweeps": info["sweeps"], "resid_2": info["resid_2"]}
+        extra["minres_solve"] = res
+        extra["fp32_ir_speedup_vs_fp64_per_solve"] = res["fp64"]["seconds"] / res["fp32_ir"]["seconds"]
+
+    # H x bandwidth at L = 28 (roofline of the hot-loop kernel)
+    peak, peak_src = peaks()
+    rf = hv_roofline(torch, hs, args.hv_L, stream)
+    f32 = rf["f32"]
+    achieved = f32["bytes"] / f32["seconds"] / 1e9
+    traffic = profiled_traffic(f"hv_l{args.hv_L}_f32")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"k_matvec<float> (H - sigma) x at L={args.hv_L}, n={f32['n']}",
+                "algorithmic_bytes_per_launch": f32["bytes"],
+                "launch_us": f32["seconds"] * 1e6, "peak_source": peak_src,
+                "f64": {"achieved": rf["f64"]["bytes"] / rf["f64"]["seconds"] / 1e9,
+                        "launch_us": rf["f64"]["seconds"] * 1e6}}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(L, K)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded disorder realisations h_j ~ U[-h, h])",
+        "config": {"workload": f"L={L} random-field Heisenberg chain, Sz=0 (dim {n}), {K} eigenpairs "
+                               f"nearest sigma=(Emin+Emax)/2, h in {{1..5}} x seeds 0..4, FP32 MINRES + "
+                               f"FP64 refinement, FP64 Lanczos with full reorthogonalisation",
+                   "L": L, "K": K, "minres_tol": args.minres_tol, "precond": "row-norm",
+                   "l2": "per-step working set 1.5 MB (L2-resident); H x roofline inputs 321 MB > L2",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "steps_detail": recs,
+        **extra,
+        "wall_seconds_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

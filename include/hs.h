@@ -176,6 +176,17 @@ hs_status hs_twist(hs_handle* hd, const double* psi_dev, int K, double* z_host);
 hs_status hs_tridiag_eig(int k, const double* alpha, const double* beta, double* theta,
                          double* Y);
 
+/* Limit the persistent MINRES solves of this handle to nsm SMs (0 = all).
+ * Independent handles on separate streams, each with a share of the SMs, then
+ * solve their systems concurrently (several disorder realisations at once).
+ * The paper runs one realisation per GPU; this is a throughput setting only. */
+hs_status hs_set_sm_budget(hs_handle* hd, int nsm);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (every launch site increments it; graph replays count their kernels).
+ * Host-only; used to report how many kernels a timed region ran. */
+unsigned long long hs_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,18 +42,20 @@ def _newer(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose=False, extra=()):
-    os.makedirs(OUTDIR, exist_ok=True)
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(verbose=False, extra=(), lib=None, objdir=None):
+    lib = lib or LIB
+    objdir = objdir or OBJDIR
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
     hdrs = _deps()
     cc = nvcc()
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OBJDIR, s.replace(".cu", ".o"))
+        obj = os.path.join(objdir, s.replace(".cu", ".o"))
         if _newer(obj, [src] + hdrs):
             jobs.append([cc, *FLAGS, *extra, "-c", src, "-o", obj])
-    objs = [os.path.join(OBJDIR, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(objdir, s.replace(".cu", ".o")) for s in SOURCES]
 
     def run(cmd):
         if verbose:
@@ -66,9 +68,9 @@ def build(verbose=False, extra=()):
 
     with cf.ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
-    if jobs or _newer(LIB, objs):
-        run([cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
-    return LIB
+    if jobs or _newer(lib, objs):
+        run([cc, *ARCH, "-shared", "-o", lib, *objs, "-lcudart"])
+    return lib
 
 
 if __name__ == "__main__":

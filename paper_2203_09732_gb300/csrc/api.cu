@@ -3,11 +3,17 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <new>
 
 #include "common.cuh"
 
+#include <atomic>
+
 namespace hs {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 hs_status fail(hs_handle* hd, hs_status st, const std::string& msg) {
   if (hd) hd->err = msg;
@@ -22,8 +28,8 @@ uint32_t binom(int n, int r) {
 }
 
 int row_grid(const hs_handle* hd) {
-  const int g = std::min<int>((int)hd->tiles.size(), hd->grid_hv);
-  return std::max(1, g);
+  const int need = ((int)hd->blocks.size() + HV_WARPS - 1) / HV_WARPS;
+  return std::max(1, std::min(need, hd->grid_hv));
 }
 
 hs_status ensure_reduce(hs_handle* hd) {
@@ -61,10 +67,10 @@ static int colex_rank(uint32_t p) {
   return r;
 }
 
-// Build low tables, blocks and tiles (see common.cuh for the layout).
+// Build the low-pattern table and the block headers (see common.cuh).
 static hs_status build_tables(hs_handle* hd) {
   const int L = hd->L, N = hd->N, k = hd->k, hb = hd->hb;
-  // classes of low patterns
+  if (hb - 1 > HD_MAX) return fail(hd, HS_BAD_ARG, "too many high bits for the block header");
   int off = 0;
   for (int w = 0; w <= k; ++w) {
     hd->cls_off[w] = off;
@@ -73,23 +79,24 @@ static hs_status build_tables(hs_handle* hd) {
   }
   const int nlow = off;  // 2^k
   hd->low.assign(nlow, LowEntry{});
-  hd->dlow64.assign(nlow, 0.0);
-  hd->nb.clear();
   std::vector<int> fill(k + 1, 0);
   for (uint32_t p = 0; p < (1u << k); ++p) {  // ascending = colex within each class
     const int w = __builtin_popcount(p);
     const int r = fill[w]++;
     const int li = hd->cls_off[w] + r;
+    LowEntry e;
+    std::memset(&e, 0, sizeof(e));
     double d = 0.0;
     int cnt = 0;
-    const size_t nb0 = hd->nb.size();
     for (int j = 0; j + 1 < k; ++j) {
       const int a = (p >> j) & 1, b = (p >> (j + 1)) & 1;
       if (a == b) {
         d += 0.25;
       } else {
         d -= 0.25;
-        hd->nb.push_back((uint16_t)colex_rank(p ^ (3u << j)));
+        const uint32_t rn = (uint32_t)colex_rank(p ^ (3u << j));
+        if (rn > 255u) return fail(hd, HS_BAD_ARG, "neighbour rank does not fit 8 bits");
+        e.nbw[cnt >> 2] |= rn << (8 * (cnt & 3));
         ++cnt;
       }
     }
@@ -99,22 +106,18 @@ static hs_status build_tables(hs_handle* hd) {
       d -= hd->h[j] * (up ? 0.5 : -0.5);
       if (up) tlow += (uint32_t)(j + 1);
     }
-    if (nb0 > 0xFFFF) return fail(hd, HS_BAD_ARG, "neighbour table overflow");
     const uint32_t code = ((p >> (k - 1)) & 1u) | ((p & 1u) << 1);
-    LowEntry e;
     e.packed = p | ((uint32_t)cnt << 16) | (code << 20) | (tlow << 24);
-    e.nb_off = (uint16_t)nb0;
     e.wrap_r = (uint16_t)colex_rank(p ^ 1u);
     e.dlow_f = (float)d;
-    e.pad = 0.f;
+    e.dlow = d;
     hd->low[li] = e;
-    hd->dlow64[li] = d;
   }
   // blocks in ascending H (= rank order)
   const uint32_t nH = 1u << hb;
   std::vector<uint32_t> Rof(nH, 0xFFFFFFFFu);
-  std::vector<BlockInfo> byH;
-  byH.reserve(nH);
+  hd->blocks.clear();
+  hd->blocks.reserve(nH);
   uint64_t R = 0;
   for (uint32_t H = 0; H < nH; ++H) {
     const int w = N - __builtin_popcount(H);
@@ -123,7 +126,6 @@ static hs_status build_tables(hs_handle* hd) {
     BlockInfo b;
     std::memset(&b, 0, sizeof(b));
     b.R = (uint32_t)R;
-    b.H = H;
     b.w = (uint8_t)w;
     b.code = (uint8_t)((H & 1u) | (((H >> (hb - 1)) & 1u) << 1));
     // cut bond (k-1, k)
@@ -152,37 +154,16 @@ static hs_status build_tables(hs_handle* hd) {
     b.nh = (uint8_t)nh;
     b.thigh = (uint8_t)(th % (uint32_t)L);
     b.dhigh = d;
-    byH.push_back(b);
+    hd->blocks.push_back(b);
+    // the wrap partner is filled below; remember H in Rwrap for now
+    hd->blocks.back().Rwrap = H;
     R += binom(k, w);
   }
   if ((long long)R != hd->n) return fail(hd, HS_BAD_ARG, "internal: block sizes do not sum to n");
-  for (auto& b : byH) {
-    const uint32_t Hw = b.H ^ (1u << (hb - 1));
+  for (auto& b : hd->blocks) {
+    const uint32_t Hw = b.Rwrap ^ (1u << (hb - 1));
     b.Rwrap = Rof[Hw] == 0xFFFFFFFFu ? 0u : Rof[Hw];
   }
-  // class-sorted block array and tiles
-  hd->blocks.clear();
-  hd->tiles.clear();
-  const long long target = std::max<long long>(
-      256, std::min<long long>(2048, hd->n / std::max(1, hd->num_sms * 4)));
-  for (int w = 0; w <= k; ++w) {
-    const int C = hd->cls_C[w];
-    const int G = (int)std::max<long long>(1, std::min<long long>(TILE_G_MAX, target / C));
-    std::vector<BlockInfo> cls;
-    for (const auto& b : byH)
-      if (b.w == w) cls.push_back(b);
-    for (size_t i = 0; i < cls.size(); i += G) {
-      Tile t;
-      t.b0 = (uint32_t)(hd->blocks.size() + i);
-      t.G = (uint16_t)std::min<size_t>(G, cls.size() - i);
-      t.w = (uint16_t)w;
-      hd->tiles.push_back(t);
-    }
-    hd->blocks.insert(hd->blocks.end(), cls.begin(), cls.end());
-  }
-  std::stable_sort(hd->tiles.begin(), hd->tiles.end(), [&](const Tile& a, const Tile& b) {
-    return hd->blocks[a.b0].H < hd->blocks[b.b0].H;
-  });
   return HS_OK;
 }
 
@@ -209,15 +190,11 @@ hs_status set_sigma_dev(hs_handle* hd, double sigma) {
 hs::Geo hs_handle::geo() const {
   hs::Geo g;
   g.low = d_low;
-  g.nb = d_nb;
-  g.dlow64 = d_dlow64;
   g.blocks = d_blocks;
-  g.tiles = d_tiles;
-  g.ntiles = (int)tiles.size();
+  g.nblocks = (int)blocks.size();
   g.k = k;
   g.L = L;
   g.nlow = (int)low.size();
-  g.nnb = (int)nb.size();
   for (int i = 0; i < hs::KLO_MAX + 2; ++i) {
     g.cls_off[i] = cls_off[i];
     g.cls_C[i] = cls_C[i] > 0 ? cls_C[i] : 1;
@@ -231,6 +208,8 @@ using namespace hs;
 extern "C" {
 
 static const char* kNullHandle = "null handle";
+
+unsigned long long hs_kernel_launches(void) { return g_launches.load(); }
 
 const char* hs_last_error(const hs_handle* hd) { return hd ? hd->err.c_str() : kNullHandle; }
 
@@ -246,7 +225,12 @@ hs_status hs_create(int L, const double* h_host, double sigma, void* cuda_stream
   if (!hd) return HS_OOM;
   hd->L = L;
   hd->N = L / 2;
-  hd->k = std::max(2, std::min(KLO_MAX, L - 4));
+  // low bits: 10 (blocks of up to 252 rows) for large chains, 8 below L = 22
+  // so that small chains still have enough blocks to spread over the GPU;
+  // HS_KLO overrides it (tuning)
+  int kk = L >= 22 ? 10 : 8;
+  if (const char* e = getenv("HS_KLO")) kk = atoi(e);
+  hd->k = std::max(2, std::min(std::min(KLO_MAX, kk), L - 2));
   hd->hb = L - hd->k;
   hd->n = (long long)binom(L, L / 2);
   for (int j = 0; j < L; ++j) hd->h[j] = h_host[j];
@@ -262,10 +246,7 @@ hs_status hs_create(int L, const double* h_host, double sigma, void* cuda_stream
   hd->grid_hv = std::min(RED_MAX_CTAS, hd->num_sms * 4);
   if ((st = build_tables(hd)) != HS_OK) return bail(st);
   if ((st = upload(hd, &hd->d_low, hd->low)) != HS_OK) return bail(st);
-  if ((st = upload(hd, &hd->d_nb, hd->nb)) != HS_OK) return bail(st);
-  if ((st = upload(hd, &hd->d_dlow64, hd->dlow64)) != HS_OK) return bail(st);
   if ((st = upload(hd, &hd->d_blocks, hd->blocks)) != HS_OK) return bail(st);
-  if ((st = upload(hd, &hd->d_tiles, hd->tiles)) != HS_OK) return bail(st);
   {
     const int W = LMAX / 2 + 2;
     std::vector<uint32_t> bt((LMAX + 1) * W);
@@ -294,10 +275,7 @@ void hs_free(hs_handle* hd) {
     if (hd->graph64[i]) cudaGraphExecDestroy(hd->graph64[i]);
   }
   cudaFree(hd->d_low);
-  cudaFree(hd->d_nb);
-  cudaFree(hd->d_dlow64);
   cudaFree(hd->d_blocks);
-  cudaFree(hd->d_tiles);
   cudaFree(hd->d_binom);
   cudaFree(hd->d_sigma);
   cudaFree(hd->d_partial);
@@ -306,10 +284,18 @@ void hs_free(hs_handle* hd) {
   cudaFree(hd->ws64);
   cudaFree(hd->d_state);
   cudaFree(hd->lz);
+  cudaFree(hd->d_smr_first);
   if (hd->h_pinned) cudaFreeHost(hd->h_pinned);
   if (hd->h_state) cudaFreeHost(hd->h_state);
   cudaGetLastError();
   delete hd;
+}
+
+hs_status hs_set_sm_budget(hs_handle* hd, int nsm) {
+  if (!hd) return HS_BAD_ARG;
+  if (nsm < 0) return fail(hd, HS_BAD_ARG, "hs_set_sm_budget: negative SM count");
+  hd->sm_budget = nsm;
+  return HS_OK;
 }
 
 hs_status hs_dim(const hs_handle* hd, long long* n_out) {

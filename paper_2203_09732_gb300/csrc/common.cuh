@@ -5,7 +5,7 @@
 //   p = s & (2^k - 1) and hb = L - k high bits H = s >> k. All states with the
 //   same H form one contiguous rank range (a "block") of C(k, w) rows,
 //   w = L/2 - popcount(H), ordered by the colex rank r of p among k-bit words of
-//   popcount w. So rank(s) = R_H + r.
+//   popcount w. So rank(s) = R_H + r, and blocks are ordered by H.
 //   Bonds of Eq. (1) fall in four kinds:
 //     low interior  (j, j+1), j + 1 < k : target stays in the block, r -> r'
 //                                         (per-pattern neighbour list);
@@ -14,7 +14,9 @@
 //     cut (k-1, k)                      : target = row + C(k-1, w-1) or
 //                                         row - C(k-1, w), per block;
 //     wrap (L-1, 0)                     : target = R_{H ^ top} + rank(p ^ 1).
-//   Low tables live in shared memory; per-block data in a tile header.
+//   One warp processes one block at a time (lane l takes rows l + 32 j); the
+//   per-pattern table lives in shared memory, the 128-byte block header is read
+//   with one coalesced load and broadcast by shuffles.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -27,21 +29,24 @@
 namespace hs {
 
 constexpr int LMAX = 32;
-constexpr int KLO_MAX = 10;            // low bits per state
+constexpr int KLO_MAX = 10;            // low bits per state (C(10, 5) = 252 rows per block)
 constexpr int NB_MAX = KLO_MAX - 1;    // low interior bonds
-constexpr int HD_MAX = LMAX - 3;       // high interior bonds (hb - 1 <= 29)
-constexpr int TILE_G_MAX = 32;         // blocks per tile
+constexpr int HD_MAX = 26;             // high interior bonds held by a block header
 constexpr int HV_THREADS = 256;
+constexpr int HV_WARPS = HV_THREADS / 32;
+constexpr int JMAX = 8;                // rows per lane per block (C <= 256)
 constexpr int RED_MAX_CTAS = 4096;     // partial-sum slots per reduction
 
-// One entry per low pattern p, indexed by off[w] + r (class w, colex rank r).
+// One entry per low pattern p, indexed by off[w] + r (class w, colex rank r); 32 bytes.
 struct LowEntry {
   uint32_t packed;   // pat (bits 0..15) | nb_cnt << 16 | code << 20 | tlow << 24
-  uint16_t nb_off;   // first neighbour in the nb list
   uint16_t wrap_r;   // colex rank of p ^ 1 in its class
+  uint16_t pad;
   float dlow_f;      // dlow rounded to FP32
-  float pad;
+  uint32_t nbw[3];   // up to 9 neighbour ranks r' (uint8 each, same class)
+  double dlow;       // Ising terms of low interior bonds + fields on low sites
 };
+static_assert(sizeof(LowEntry) == 32, "LowEntry is 32 bytes");
 // code = bit (k-1) of p | bit 0 of p << 1; tlow = sum of (j + 1) over set bits j < k.
 
 __host__ __device__ inline uint32_t le_pat(uint32_t pk) { return pk & 0xFFFFu; }
@@ -49,40 +54,28 @@ __host__ __device__ inline int le_cnt(uint32_t pk) { return (pk >> 16) & 0xF; }
 __host__ __device__ inline uint32_t le_code(uint32_t pk) { return (pk >> 20) & 0x3; }
 __host__ __device__ inline uint32_t le_tlow(uint32_t pk) { return pk >> 24; }
 
-// One entry per valid high pattern H (160 bytes; copied to shared memory as
-// 40 words per tile block).
+// One 128-byte header per valid high pattern H, in rank order (ascending H).
+// Word layout (read by lane = word index): 0 R, 1 Rwrap, 2 bdelta,
+// 3 w | nh << 8 | code << 16 | thigh << 24, 4-5 dhigh, 6.. hd[].
 struct BlockInfo {
   uint32_t R;        // rank of the block's first row
   uint32_t Rwrap;    // first row of block H ^ top (only read when the wrap bond flips)
   int32_t bdelta;    // row offset of the cut-bond (k-1, k) flip
-  uint32_t H;
   uint8_t w;         // low popcount
   uint8_t nh;        // antiparallel high interior bonds
   uint8_t code;      // bit 0 of H | top bit of H << 1
   uint8_t thigh;     // sum of (j + 1) over set high bits j >= k, mod L
-  float dhs_f;       // shared-memory copy only: (float)(dhigh - sigma)
   double dhigh;      // Ising terms of high interior bonds + fields on high sites
-  double dhs;        // shared-memory copy only: dhigh - sigma
   int32_t hd[HD_MAX];  // row offsets of the antiparallel high interior flips
-  int32_t pad;
 };
-static_assert(sizeof(BlockInfo) % 8 == 0, "BlockInfo must be a whole number of words");
+static_assert(sizeof(BlockInfo) == 128, "BlockInfo is 128 bytes");
 
-struct Tile {
-  uint32_t b0;       // first block (index into the class-sorted block array)
-  uint16_t G;        // blocks in the tile (all of class w)
-  uint16_t w;
-};
-
-// Everything a row-loop kernel needs, passed by value.
+// Everything a row kernel needs, passed by value.
 struct Geo {
   const LowEntry* low;
-  const uint16_t* nb;
-  const double* dlow64;
   const BlockInfo* blocks;
-  const Tile* tiles;
-  int ntiles;
-  int k, L, nlow, nnb;
+  int nblocks;
+  int k, L, nlow;
   int cls_off[KLO_MAX + 2];
   int cls_C[KLO_MAX + 2];
   uint32_t n;
@@ -106,11 +99,6 @@ struct MinresState {
   int pad;
 };
 
-struct Reduce {                      // last-CTA reduction scratch
-  double* partial;                   // RED_MAX_CTAS * 4 doubles
-  unsigned int* counter;             // one counter per pass kind
-};
-
 }  // namespace hs
 
 // The opaque handle of the C ABI.
@@ -125,22 +113,16 @@ struct hs_handle {
 
   // host tables
   std::vector<hs::LowEntry> low;
-  std::vector<double> dlow64;
-  std::vector<uint16_t> nb;
   std::vector<hs::BlockInfo> blocks;
-  std::vector<hs::Tile> tiles;
   int cls_off[hs::KLO_MAX + 2] = {0};
   int cls_C[hs::KLO_MAX + 2] = {0};
 
   // device copies
   hs::LowEntry* d_low = nullptr;
-  uint16_t* d_nb = nullptr;
-  double* d_dlow64 = nullptr;
   hs::BlockInfo* d_blocks = nullptr;
-  hs::Tile* d_tiles = nullptr;
   uint32_t* d_binom = nullptr;       // (LMAX + 1) x (LMAX / 2 + 2)
   double* d_sigma = nullptr;         // device copy of sigma
-  int grid_hv = 0;                   // persistent grid of the row kernels
+  int grid_hv = 0;                   // grid of the row kernels
 
   // reductions
   double* d_partial = nullptr;
@@ -154,7 +136,11 @@ struct hs_handle {
   hs::MinresState* h_state = nullptr;  // pinned
   cudaGraphExec_t graph32[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t graph64[3] = {nullptr, nullptr, nullptr};
-  int graph_iters = 0;
+
+  // shared-memory-resident MINRES plan
+  int sm_budget = 0;                 // SMs a persistent solve may use (0 = all)
+  int smr_grid = 0, smr_rows_cap = 0, smr_hdr_cap = 0;
+  int* d_smr_first = nullptr;
 
   // Lanczos workspace
   double* lz = nullptr; size_t lz_vectors = 0;
@@ -163,6 +149,9 @@ struct hs_handle {
 };
 
 namespace hs {
+
+// launch accounting -----------------------------------------------------------
+void count_launches(unsigned long long k);
 
 // error helpers -------------------------------------------------------------
 hs_status fail(hs_handle* hd, hs_status st, const std::string& msg);

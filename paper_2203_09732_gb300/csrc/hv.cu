@@ -6,31 +6,23 @@
 namespace hs {
 
 // ---------------------------------------------------------------------------
-// y = (H - sigma * shifted) x. Persistent CTAs walk the tiles in rank order.
+// y = (H - sigma * shifted) x. Warps walk the blocks in rank order.
 template <typename T>
 __global__ void __launch_bounds__(HV_THREADS) k_matvec(Geo g, const T* __restrict__ x,
                                                        T* __restrict__ y, const double* d_sigma,
                                                        int shifted) {
   extern __shared__ __align__(16) char smem[];
-  RowSmem s = row_smem_carve(smem, g);
-  constexpr bool is64 = sizeof(T) == 8;
-  row_smem_fill(s, g, is64);
+  const RowSmem<T> s = row_smem_setup<T>(smem, g);
   const double sigma = shifted ? *d_sigma : 0.0;
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    const Tile tl = g.tiles[t];
-    __syncthreads();
-    tile_load(s, g, tl, sigma);
-    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
-      const LowEntry e = s.low[li];
-      const uint32_t xc = cut_mask(e, b);
-      T xi;
-      const T off = offdiag_row<T>(x, s, b, e, (uint32_t)r, xc, xi);
-      T a;
-      if constexpr (is64) a = diag_d(s.dlow64[li], b, xc);
-      else a = diag_f(e, b, xc);
-      y[b.R + r] = a * xi + off;
-    });
-  }
+  const int lane = threadIdx.x & 31;
+  for_blocks(g, sigma, [&](const Hdr& h) {
+    T xi[JMAX], hx[JMAX];
+    block_hv<T>(x, s, h, xi, hx);
+    T* yb = y + h.R + lane;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j)
+      if (j < h.J && lane + 32 * j < h.C) __stcs(yb + 32 * j, hx[j]);
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -79,26 +71,23 @@ __global__ void k_rank(const uint32_t* __restrict__ binom, int L, int N,
 __global__ void __launch_bounds__(HV_THREADS) k_diag(Geo g, double* diag, double* minv, int pc,
                                                      const double* d_sigma) {
   extern __shared__ __align__(16) char smem[];
-  RowSmem s = row_smem_carve(smem, g);
-  row_smem_fill(s, g, true);
+  const RowSmem<double> s = row_smem_setup<double>(smem, g);
   const double sigma = *d_sigma;
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    const Tile tl = g.tiles[t];
-    __syncthreads();
-    tile_load(s, g, tl, sigma);
-    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
-      const LowEntry e = s.low[li];
-      const uint32_t xc = cut_mask(e, b);
-      const double am = diag_d(s.dlow64[li], b, xc);
-      const uint32_t i = b.R + r;
+  const int lane = threadIdx.x & 31;
+  for_blocks(g, sigma, [&](const Hdr& h) {
+    for (int r = lane; r < h.C; r += 32) {
+      const LowEntry& e = s.low[h.off + r];
+      const uint32_t xc = cut_mask(e.packed, h);
+      const double am = diag_d(e, h, xc);
+      const uint32_t i = h.R + r;
       if (diag) diag[i] = am + sigma;
       if (minv) {
-        const int naf = naf_row(e, b, xc);
-        double m = pc == 0 ? 1.0 : (pc == 1 ? fabs(am) : sqrt(am * am + 0.25 * naf));
+        const int naf = naf_row(e.packed, h, xc);
+        const double m = pc == 0 ? 1.0 : (pc == 1 ? fabs(am) : sqrt(am * am + 0.25 * naf));
         minv[i] = 1.0 / m;
       }
-    });
-  }
+    }
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -111,39 +100,40 @@ __global__ void __launch_bounds__(HV_THREADS) k_resid64(Geo g, const double* __r
                                                         const double* d_sigma,
                                                         double* partial) {
   extern __shared__ __align__(16) char smem[];
-  RowSmem s = row_smem_carve(smem, g);
-  row_smem_fill(s, g, true);
+  const RowSmem<double> s = row_smem_setup<double>(smem, g);
   const double sigma = *d_sigma;
+  const int lane = threadIdx.x & 31;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    const Tile tl = g.tiles[t];
-    __syncthreads();
-    tile_load(s, g, tl, sigma);
-    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
-      const LowEntry e = s.low[li];
-      const uint32_t xc = cut_mask(e, b);
-      double xi;
-      const double off = offdiag_row<double>(x, s, b, e, (uint32_t)r, xc, xi);
-      const double am = diag_d(s.dlow64[li], b, xc);
-      const uint32_t i = b.R + r;
-      const double bi = bv[i];
-      const double ri = bi - (am * xi + off);
-      rv[i] = ri;
-      const double m = precond_d<PC>(am, naf_row(e, b, xc));
-      acc[0] += ri * ri / m;
-      acc[1] += ri * ri;
-      acc[2] += bi * bi / m;
-      acc[3] += bi * bi;
-    });
-  }
+  for_blocks(g, sigma, [&](const Hdr& h) {
+    double xi[JMAX], hx[JMAX];
+    block_hv<double>(x, s, h, xi, hx);
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+      const int r = lane + 32 * j;
+      if (j < h.J && r < h.C) {
+        const LowEntry& e = s.low[h.off + r];
+        const uint32_t xc = cut_mask(e.packed, h);
+        const double m = precond_t<PC, double>(diag_d(e, h, xc), naf_row(e.packed, h, xc));
+        const uint32_t i = h.R + r;
+        const double bi_ = bv[i];
+        const double ri = bi_ - hx[j];
+        rv[i] = ri;
+        acc[0] += ri * ri / m;
+        acc[1] += ri * ri;
+        acc[2] += bi_ * bi_ / m;
+        acc[3] += bi_ * bi_;
+      }
+    }
+  });
   block_sum<4>(acc, s.red);
   if (threadIdx.x == 0)
     for (int j = 0; j < 4; ++j) partial[blockIdx.x * 4 + j] = acc[j];
 }
 
 // ---------------------------------------------------------------------------
+template <typename T>
 static size_t smem_of(const hs_handle* hd) {
-  return row_smem_bytes((int)hd->low.size(), (int)hd->nb.size());
+  return row_smem_bytes<T>((int)hd->low.size());
 }
 
 template <typename K>
@@ -156,16 +146,17 @@ static hs_status prep_smem(hs_handle* hd, K kern, size_t bytes) {
 
 hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted) {
   const Geo g = hd->geo();
-  const size_t sm = smem_of(hd);
   const int grid = row_grid(hd);
   if (dt == HS_F32) {
+    const size_t sm = smem_of<float>(hd);
     if (prep_smem(hd, k_matvec<float>, sm) != HS_OK) return HS_CUDA;
     k_matvec<float><<<grid, HV_THREADS, sm, hd->stream>>>(
-        g, static_cast<const float*>(x), static_cast<float*>(y), hd->d_sigma, shifted);
+        g, static_cast<const float*>(x), static_cast<float*>(y), hd->d_sigma, shifted); count_launches(1);
   } else {
+    const size_t sm = smem_of<double>(hd);
     if (prep_smem(hd, k_matvec<double>, sm) != HS_OK) return HS_CUDA;
     k_matvec<double><<<grid, HV_THREADS, sm, hd->stream>>>(
-        g, static_cast<const double*>(x), static_cast<double*>(y), hd->d_sigma, shifted);
+        g, static_cast<const double*>(x), static_cast<double*>(y), hd->d_sigma, shifted); count_launches(1);
   }
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
@@ -174,7 +165,7 @@ hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int 
 hs_status launch_unrank(hs_handle* hd, long long first, long long count, unsigned int* out) {
   if (count <= 0) return HS_OK;
   const int grid = (int)std::min<long long>((count + 255) / 256, hd->num_sms * 8LL);
-  k_unrank<<<grid, 256, 0, hd->stream>>>(hd->d_binom, hd->L, hd->N, first, count, out);
+  k_unrank<<<grid, 256, 0, hd->stream>>>(hd->d_binom, hd->L, hd->N, first, count, out); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }
@@ -182,16 +173,16 @@ hs_status launch_unrank(hs_handle* hd, long long first, long long count, unsigne
 hs_status launch_rank(hs_handle* hd, const unsigned int* st, long long count, long long* out) {
   if (count <= 0) return HS_OK;
   const int grid = (int)std::min<long long>((count + 255) / 256, hd->num_sms * 8LL);
-  k_rank<<<grid, 256, 0, hd->stream>>>(hd->d_binom, hd->L, hd->N, st, count, out);
+  k_rank<<<grid, 256, 0, hd->stream>>>(hd->d_binom, hd->L, hd->N, st, count, out); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }
 
 hs_status launch_diag(hs_handle* hd, double* diag, hs_precond pc, double* minv) {
-  const size_t sm = smem_of(hd);
+  const size_t sm = smem_of<double>(hd);
   if (prep_smem(hd, k_diag, sm) != HS_OK) return HS_CUDA;
   k_diag<<<row_grid(hd), HV_THREADS, sm, hd->stream>>>(hd->geo(), diag, minv, (int)pc,
-                                                       hd->d_sigma);
+                                                       hd->d_sigma); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }
@@ -200,21 +191,21 @@ hs_status resid64(hs_handle* hd, const double* b, const double* x, double* r, hs
                   double sums_out[4]) {
   hs_status st = ensure_reduce(hd);
   if (st != HS_OK) return st;
-  const size_t sm = smem_of(hd);
+  const size_t sm = smem_of<double>(hd);
   const int grid = row_grid(hd);
   const Geo g = hd->geo();
   switch (pc) {
     case HS_PC_ID:
       if (prep_smem(hd, k_resid64<0>, sm) != HS_OK) return HS_CUDA;
-      k_resid64<0><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial);
+      k_resid64<0><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
       break;
     case HS_PC_JACOBI:
       if (prep_smem(hd, k_resid64<1>, sm) != HS_OK) return HS_CUDA;
-      k_resid64<1><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial);
+      k_resid64<1><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
       break;
     default:
       if (prep_smem(hd, k_resid64<2>, sm) != HS_OK) return HS_CUDA;
-      k_resid64<2><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial);
+      k_resid64<2><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
       break;
   }
   HS_CUDA_TRY(hd, cudaGetLastError());

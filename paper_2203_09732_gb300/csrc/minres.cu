@@ -14,6 +14,7 @@
 // Vectors: q (2, ping-pong by k parity), d (2), p, x.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 
 #include "rows.cuh"
@@ -24,56 +25,39 @@ struct MinresVecs {
   void* q0; void* q1; void* d0; void* d1; void* p; void* x;
 };
 
-template <int PC>
-__device__ __forceinline__ float pc_mf(const LowEntry& e, const BlockInfo& b, uint32_t xc,
-                                       float& am) {
-  am = diag_f(e, b, xc);
-  return precond_f<PC>(am, naf_row(e, b, xc));
-}
-template <int PC>
-__device__ __forceinline__ double pc_md(double dlow, const LowEntry& e, const BlockInfo& b,
-                                        uint32_t xc, double& am) {
-  am = diag_d(dlow, b, xc);
-  return precond_d<PC>(am, naf_row(e, b, xc));
-}
-
-template <typename T, int PC>
-__device__ __forceinline__ T row_m(const RowSmem& s, const LowEntry& e, const BlockInfo& b,
-                                   uint32_t xc, int li, T& am) {
-  if constexpr (sizeof(T) == 8) return pc_md<PC>(s.dlow64[li], e, b, xc, am);
-  else return pc_mf<PC>(e, b, xc, am);
-}
-
 // ---------------------------------------------------------------------------
 // Row passes shared by the per-pass kernels and the persistent kernel. Each
-// returns this thread's contribution to the pass's reduction.
+// adds this thread's contribution to the pass's reduction into acc.
 template <typename T, int PC>
-__device__ __forceinline__ void rows_init(const Geo& g, const RowSmem& s, double sigma,
+__device__ __forceinline__ T row_m(const LowEntry& e, const Hdr& h, T& am) {
+  const uint32_t xc = cut_mask(e.packed, h);
+  am = diag_t<T>(e, h, xc);
+  return precond_t<PC, T>(am, naf_row(e.packed, h, xc));
+}
+
+template <typename T, int PC>
+__device__ __forceinline__ void rows_init(const Geo& g, const RowSmem<T>& s, double sigma,
                                           const T* __restrict__ bv, const MinresVecs& v, T& acc,
                                           int& zero_m) {
   T* q0 = (T*)v.q0; T* q1 = (T*)v.q1; T* d0 = (T*)v.d0; T* d1 = (T*)v.d1; T* x = (T*)v.x;
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    const Tile tl = g.tiles[t];
-    __syncthreads();
-    tile_load(s, g, tl, sigma);
-    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
-      const LowEntry e = s.low[li];
-      const uint32_t xc = cut_mask(e, b);
+  const int lane = threadIdx.x & 31;
+  for_blocks(g, sigma, [&](const Hdr& h) {
+    for (int r = lane; r < h.C; r += 32) {
       T am;
-      const T m = row_m<T, PC>(s, e, b, xc, li, am);
-      const uint32_t i = b.R + r;
-      const T bi = bv[i];
+      const T m = row_m<T, PC>(s.low[h.off + r], h, am);
+      const uint32_t i = h.R + r;
+      const T b = bv[i];
       zero_m += (m == T(0));
-      const T q = m == T(0) ? T(0) : bi / m;
+      const T q = m == T(0) ? T(0) : b / m;
       q1[i] = q; q0[i] = T(0); d0[i] = T(0); d1[i] = T(0); x[i] = T(0);
-      acc += q * bi;
-    });
-  }
+      acc += q * b;
+    }
+  });
 }
 
 // pass A_k: optional pending d/x update of iteration k-1, then p = (H - sigma) q_k.
-template <typename T>
-__device__ __forceinline__ void rows_A(const Geo& g, const RowSmem& s, double sigma,
+template <typename T, bool COH>
+__device__ __forceinline__ void rows_A(const Geo& g, const RowSmem<T>& s, double sigma,
                                        const MinresVecs& v, long long k, bool doC, bool doMV,
                                        T cq, T cd1, T cd2, T tau, T& acc) {
   const bool odd = (k & 1) != 0;
@@ -83,58 +67,51 @@ __device__ __forceinline__ void rows_A(const Geo& g, const RowSmem& s, double si
   T* dB = (T*)(odd ? v.d0 : v.d1);               // d_{k-3} -> d_{k-1}
   T* p = (T*)v.p;
   T* x = (T*)v.x;
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    const Tile tl = g.tiles[t];
-    __syncthreads();
-    tile_load(s, g, tl, sigma);
-    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
-      const uint32_t i = b.R + r;
-      if (doC) {
+  const int lane = threadIdx.x & 31;
+  for_blocks(g, sigma, [&](const Hdr& h) {
+    if (doC) {
+      for (int r = lane; r < h.C; r += 32) {
+        const uint32_t i = h.R + r;
         const T d = cq * qp[i] + cd1 * dA[i] + cd2 * dB[i];
         dB[i] = d;
         x[i] += tau * d;
       }
-      if (doMV) {
-        const LowEntry e = s.low[li];
-        const uint32_t xc = cut_mask(e, b);
-        T xi;
-        const T off = offdiag_row<T>(qc, s, b, e, (uint32_t)r, xc, xi);
-        T a;
-        if constexpr (sizeof(T) == 8) a = diag_d(s.dlow64[li], b, xc);
-        else a = diag_f(e, b, xc);
-        const T pi = a * xi + off;
-        p[i] = pi;
-        acc += xi * pi;
+    }
+    if (doMV) {
+      T xi[JMAX], hx[JMAX];
+      block_hv<T, COH>(qc, s, h, xi, hx);
+#pragma unroll
+      for (int j = 0; j < JMAX; ++j) {
+        const int r = lane + 32 * j;
+        if (j < h.J && r < h.C) {
+          p[h.R + r] = hx[j];
+          acc += xi[j] * hx[j];
+        }
       }
-    });
-  }
+    }
+  });
 }
 
 // pass B_k: q_{k+1} = M^-1 p / beta_k - (alpha_k / beta_k) q_k - (beta_k / beta_{k-1}) q_{k-1}
 template <typename T, int PC>
-__device__ __forceinline__ void rows_B(const Geo& g, const RowSmem& s, double sigma,
+__device__ __forceinline__ void rows_B(const Geo& g, const RowSmem<T>& s, double sigma,
                                        const MinresVecs& v, long long k, T c1, T c2, T c3,
                                        T& acc) {
   const bool odd = (k & 1) != 0;
   const T* qc = (const T*)(odd ? v.q1 : v.q0);   // q_k
   T* qn = (T*)(odd ? v.q0 : v.q1);               // q_{k-1} -> q_{k+1}
   const T* p = (const T*)v.p;
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    const Tile tl = g.tiles[t];
-    __syncthreads();
-    tile_load(s, g, tl, sigma);
-    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
-      const uint32_t i = b.R + r;
+  const int lane = threadIdx.x & 31;
+  for_blocks(g, sigma, [&](const Hdr& h) {
+    for (int r = lane; r < h.C; r += 32) {
+      const uint32_t i = h.R + r;
       T m = T(1), am;
-      if (PC != 0) {
-        const LowEntry e = s.low[li];
-        m = row_m<T, PC>(s, e, b, cut_mask(e, b), li, am);
-      }
+      if (PC != 0) m = row_m<T, PC>(s.low[h.off + r], h, am);
       const T q = (p[i] / m) * c1 - c2 * qc[i] - c3 * qn[i];
       qn[i] = q;
       acc += m * q * q;
-    });
-  }
+    }
+  });
 }
 
 // Scalar part of pass B (Givens rotation of Algorithm 2), on one thread.
@@ -231,6 +208,67 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb, unsigned long long 
   return s_ok != 0;
 }
 
+// Reduction + barrier in one step: CTA c publishes its two partial sums and the
+// reduction's generation number in slot c (release store, after a fence that
+// also publishes the CTA's other global writes); warp 0 of every CTA polls all
+// slots with acquire loads until each carries the generation, then adds them in
+// a fixed order (lane-strided sums and a fixed shuffle tree), so every CTA ends
+// with identical totals. Slots alternate between two buffers by generation
+// parity. The wait gives up after `limit` polls (HS_TIMEOUT).
+struct Slot {
+  double v0, v1;
+  unsigned gen;
+  unsigned pad[3];
+};
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool slot_reduce(Slot* slots, int G, unsigned gen, double v0, double v1,
+                                            double (&tot)[2], unsigned long long limit, int* err,
+                                            double* sbuf) {
+  __shared__ int s_ok;
+  Slot* buf = slots + (size_t)(gen & 1u) * G;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    buf[blockIdx.x].v0 = v0;
+    buf[blockIdx.x].v1 = v1;
+    __threadfence();
+    st_release_u32(&buf[blockIdx.x].gen, gen);
+  }
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int ok = 1;
+    double a0 = 0.0, a1 = 0.0;
+    unsigned long long it = 0;
+    while (true) {
+      bool mine = true;
+      a0 = 0.0;
+      a1 = 0.0;
+      for (int c = lane; c < G; c += 32) {
+        if (ld_acquire_u32(&buf[c].gen) != gen) { mine = false; break; }
+        a0 += __ldcg(&buf[c].v0);
+        a1 += __ldcg(&buf[c].v1);
+      }
+      if (__all_sync(0xffffffffu, mine)) break;
+      if (++it > limit) { ok = 0; if (lane == 0) atomicExch(err, 1); break; }
+      if ((it & 255ull) == 0 && ld_relaxed_i32(err)) { ok = 0; break; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane == 0) { sbuf[0] = a0; sbuf[1] = a1; s_ok = ok; }
+  }
+  __syncthreads();
+  tot[0] = sbuf[0];
+  tot[1] = sbuf[1];
+  return s_ok != 0;
+}
+
 // Sum the per-CTA partials (NV values, stride 2) in a fixed order; thread 0..31
 // of every CTA compute the same totals. Result broadcast through shared memory.
 template <int NV>
@@ -265,8 +303,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_persist(Geo g, const T* _
   extern __shared__ __align__(16) char smem[];
   __shared__ MinresState S;
   __shared__ double sbuf[4];
-  RowSmem s = row_smem_carve(smem, g);
-  row_smem_fill(s, g, sizeof(T) == 8);
+  const RowSmem<T> s = row_smem_setup<T>(smem, g);
   const double sigma = *d_sigma;
   const int G = gridDim.x;
   int red = 0;   // reduction counter -> partial buffer parity
@@ -294,7 +331,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_persist(Geo g, const T* _
     // pass A
     const bool doC = S.pending != 0, doMV = S.done == 0;
     T acc = T(0);
-    rows_A<T>(g, s, sigma, v, S.k, doC, doMV, (T)S.cq, (T)S.cd1, (T)S.cd2, (T)S.tau, acc);
+    rows_A<T, true>(g, s, sigma, v, S.k, doC, doMV, (T)S.cq, (T)S.cd1, (T)S.cd2, (T)S.tau, acc);
     if (!doMV) {                       // the final pending update only
       __syncthreads();
       if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
@@ -325,6 +362,402 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_persist(Geo g, const T* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Shared-memory-resident persistent form, for problems whose per-SM share of
+// the vectors fits on chip (L <= 20 in FP64, L <= 22 in FP32). One CTA per SM
+// owns a contiguous range of blocks; its rows of p, d_{k-1}, d_{k-2}, x and of
+// both q iterates stay in shared memory for the whole solve, so the only
+// global traffic per iteration is the gather of q_k for the off-diagonal
+// terms and the write of q_{k+1}. Same arithmetic, same order as the other
+// forms (rows_* above).
+
+// Rows of one block whose own segment (self and low-interior neighbours) is
+// read from shared memory xl; the other gathers come from global xg.
+template <typename T, int JM>
+__device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* xl,
+                                             const LowEntry* low, const Hdr& h, T (&xi)[JM],
+                                             T (&hx)[JM]) {
+  const int lane = threadIdx.x & 31;
+  const T* xb = xg + h.R;
+  T side[JM];
+#pragma unroll
+  for (int j = 0; j < JM; ++j) {
+    xi[j] = T(0);
+    side[j] = T(0);
+    hx[j] = T(0);
+    const int r = lane + 32 * j;
+    if (j < h.J && r < h.C) {
+      const LowEntry& e = low[h.off + r];
+      const uint32_t xc = cut_mask(e.packed, h);
+      xi[j] = xl[r];
+      const T c1 = (xc & 1u) ? ldx<T, true>(xb + h.bdelta + r) : T(0);
+      const T c2 = (xc & 2u) ? ldx<T, true>(xg + (h.Rwrap + e.wrap_r)) : T(0);
+      side[j] = c1 + c2;
+    }
+  }
+  constexpr int HG = 4;
+  for (int m0 = 0; m0 < h.nh; m0 += HG) {
+    T v[HG][JM];
+#pragma unroll
+    for (int mm = 0; mm < HG; ++mm) {
+      const bool on = m0 + mm < h.nh;
+      const T* xh = xb + (on ? hdr_hd(h, m0 + mm) : 0) + lane;
+#pragma unroll
+      for (int j = 0; j < JM; ++j)
+        v[mm][j] = (on && j < h.J && lane + 32 * j < h.C) ? ldx<T, true>(xh + 32 * j) : T(0);
+    }
+#pragma unroll
+    for (int mm = 0; mm < HG; ++mm)
+#pragma unroll
+      for (int j = 0; j < JM; ++j) hx[j] += v[mm][j];
+  }
+#pragma unroll
+  for (int j = 0; j < JM; ++j) {
+    const int r = lane + 32 * j;
+    if (j < h.J && r < h.C) {
+      const LowEntry& e = low[h.off + r];
+      const uint32_t pk = e.packed;
+      const uint32_t xc = cut_mask(pk, h);
+      T acc = hx[j] + side[j];
+      const int cnt = le_cnt(pk);
+      const uint32_t w0 = e.nbw[0], w1 = e.nbw[1], w2 = e.nbw[2];
+#pragma unroll
+      for (int m = 0; m < NB_MAX; ++m) {
+        const uint32_t wd = m < 4 ? w0 : (m < 8 ? w1 : w2);
+        if (m < cnt) acc += xl[(wd >> (8 * (m & 3))) & 0xFFu];
+      }
+      hx[j] = diag_t<T>(e, h, xc) * xi[j] + T(0.5) * acc;
+    }
+  }
+}
+
+// CTA-wide sum of two per-thread values; totals land in every lane of warp 0.
+// FP32 values are reduced in FP32 within warps (one FP64 add tree of 32 warp
+// sums follows); FP64 values go through shared memory so that one warp does the
+// FP64 additions (FP64 throughput on this part is a small fraction of FP32).
+template <typename T>
+__device__ __forceinline__ void cta_sum2(T a, T b, double* stmp, double& o0, double& o1) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { stmp[2 * wid] = (double)a; stmp[2 * wid + 1] = (double)b; }
+    __syncthreads();
+    if (wid == 0) {
+      o0 = lane < nw ? stmp[2 * lane] : 0.0;
+      o1 = lane < nw ? stmp[2 * lane + 1] : 0.0;
+    }
+  } else {
+    stmp[threadIdx.x] = a;
+    stmp[blockDim.x + threadIdx.x] = b;
+    __syncthreads();
+    if (wid == 0) {
+      o0 = 0.0;
+      o1 = 0.0;
+      for (int i = lane; i < (int)blockDim.x; i += 32) {
+        o0 += stmp[i];
+        o1 += stmp[blockDim.x + i];
+      }
+    }
+  }
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      o0 += __shfl_xor_sync(0xffffffffu, o0, o);
+      o1 += __shfl_xor_sync(0xffffffffu, o1, o);
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Slot reduction for grids of at most 256 CTAs, called by warp 0 with the
+// CTA's totals in (c0, c1): publish, poll every slot with independent relaxed
+// loads, one acquire fence, then a fixed-order sum (identical in every CTA).
+__device__ __forceinline__ bool slot_reduce_w0(Slot* slots, int G, unsigned gen, double c0,
+                                               double c1, double (&tot)[2],
+                                               unsigned long long limit, int* err) {
+  const int lane = threadIdx.x & 31;
+  Slot* buf = slots + (size_t)(gen & 1u) * G;
+  if (lane == 0) {
+    buf[blockIdx.x].v0 = c0;
+    buf[blockIdx.x].v1 = c1;
+    st_release_u32(&buf[blockIdx.x].gen, gen);   // orders the partials and, after the
+  }                                              // CTA barrier, the CTA's vector stores
+  int ok = 1;
+  unsigned long long it = 0;
+  while (true) {
+    unsigned gv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = lane + 32 * q;
+      gv[q] = c < G ? ld_relaxed_u32(&buf[c].gen) : gen;
+    }
+    bool mine = true;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) mine = mine && (gv[q] == gen);
+    if (__all_sync(0xffffffffu, mine)) break;
+    if (++it > limit) { ok = 0; if (lane == 0) atomicExch(err, 1); break; }
+    if ((it & 255ull) == 0 && ld_relaxed_i32(err)) { ok = 0; break; }
+  }
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
+  double a0 = 0.0, a1 = 0.0;
+  if (ok) {
+    double v0[8], v1[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int c = lane + 32 * q;
+      v0[q] = c < G ? __ldcg(&buf[c].v0) : 0.0;
+      v1[q] = c < G ? __ldcg(&buf[c].v1) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { a0 += v0[q]; a1 += v1[q]; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+  }
+  tot[0] = a0;
+  tot[1] = a1;
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+template <typename T>
+__host__ __device__ inline size_t smr_bytes(int nlow, int hdr_cap, int rows_cap, int nt) {
+  size_t b = sizeof(LowEntry) * (size_t)nlow + 128 * (size_t)hdr_cap;
+  b = (b + 15) & ~size_t(15);
+  b += 8 * sizeof(T) * (size_t)rows_cap;
+  b = (b + 15) & ~size_t(15);
+  return b + sizeof(double) * (sizeof(T) == 8 ? 2 * (size_t)nt : 64);
+}
+
+// Scalar recurrences of Algorithm 2 on one thread, with one reciprocal per
+// divisor (FP64 division and square root are slow here): same quantities as
+// givens_update.
+__device__ __forceinline__ void givens_fast(MinresState& S, double sumsq, double& ib) {
+  const double bn = sumsq >= 0.0 ? sqrt(sumsq) : NAN;        // beta_{k+1}
+  const double a = S.alpha, bk = S.beta;
+  const double cp = S.c_prev, sp = S.s_prev, dh = S.delta_hat, eps = S.eps;
+  const double delta = cp * dh + sp * a;                     // delta_k
+  const double gh = -sp * dh + cp * a;                       // hat gamma_k
+  const double gamma = sqrt(gh * gh + bn * bn);              // gamma_k
+  if (!isfinite(bn) || !isfinite(gamma)) {
+    S.status = HS_NONFINITE; S.done = 2; S.pending = 0;
+    return;
+  }
+  if (gamma == 0.0) {
+    S.status = HS_BREAKDOWN; S.done = 2; S.pending = 0;
+    return;
+  }
+  const double rg = 1.0 / gamma;
+  const double c = gh * rg, sn = bn * rg;                    // c_k, s_k
+  S.tau = c * S.phi;                                         // tau_k
+  S.phi = -sn * S.phi;                                       // phi_k
+  S.cq = rg * ib;                                            // 1 / (beta_k gamma_k)
+  S.cd1 = -delta * rg;
+  S.cd2 = -eps * rg;
+  S.pending = 1;
+  S.eps = sp * bn;                                           // epsilon_{k+1}
+  S.delta_hat = cp * bn;                                     // hat delta_{k+1}
+  S.beta_prev = bk; S.beta = bn;
+  S.c_prev = c; S.s_prev = sn;
+  S.k = S.k + 1;
+  ib = bn > 0.0 ? 1.0 / bn : 0.0;
+  if (fabs(S.phi) < S.tol_abs || bn == 0.0 || S.k > S.kmax) S.done = 1;
+}
+
+template <typename T, int PC, int JM, int NT>
+__global__ void __launch_bounds__(NT, 1) k_minres_smem(
+    Geo g, const T* __restrict__ bv, T* qg0, T* qg1, T* xout, MinresState* st, double tol,
+    long long kmax, const double* d_sigma, double* part, GridBar gb, unsigned long long limit,
+    const int* __restrict__ cta_first, int rows_cap, unsigned long long* trace) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ MinresState S;
+  __shared__ double sbuf[4];
+  __shared__ double s_ib, s_ibp;
+  __shared__ int s_ok;
+  LowEntry* low = reinterpret_cast<LowEntry*>(smem);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(g.low);
+    uint4* dst = reinterpret_cast<uint4*>(low);
+    for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  const int b0 = cta_first[blockIdx.x], nbk = cta_first[blockIdx.x + 1] - b0;
+  uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * g.nlow);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
+    for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
+  }
+  size_t off = sizeof(LowEntry) * g.nlow + 128 * (size_t)nbk;
+  off = (off + 15) & ~size_t(15);
+  T* QL0 = reinterpret_cast<T*>(smem + off);
+  T* QL1 = QL0 + rows_cap;
+  T* P = QL0 + 2 * rows_cap;
+  T* D0 = QL0 + 3 * rows_cap;
+  T* D1 = QL0 + 4 * rows_cap;
+  T* X = QL0 + 5 * rows_cap;
+  T* MV = QL0 + 6 * rows_cap;        // M_ii
+  T* MI = QL0 + 7 * rows_cap;        // 1 / M_ii
+  off += 8 * sizeof(T) * (size_t)rows_cap;
+  off = (off + 15) & ~size_t(15);
+  double* stmp = reinterpret_cast<double*>(smem + off);
+  const uint32_t Rbase = __ldg(&g.blocks[b0].R);
+  const double sigma = *d_sigma;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  auto each_block = [&](auto&& f) {
+    for (int lb = wid; lb < nbk; lb += NT / 32) {
+      const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+      f(h, h.R - Rbase);
+    }
+  };
+  const int G = gridDim.x;
+  unsigned gen = 0;
+  Slot* slots = reinterpret_cast<Slot*>(part);
+  auto reduce = [&](T a, T b, double (&tot)[2]) -> bool {
+    double c0, c1;
+    cta_sum2<T>(a, b, stmp, c0, c1);
+    ++gen;
+    if (wid == 0) {
+      double t[2];
+      const bool okw = slot_reduce_w0(slots, G, gen, c0, c1, t, limit, gb.err);
+      if (lane == 0) { sbuf[0] = t[0]; sbuf[1] = t[1]; s_ok = okw; }
+    }
+    __syncthreads();
+    tot[0] = sbuf[0];
+    tot[1] = sbuf[1];
+    return s_ok != 0;
+  };
+  bool ok;
+  {
+    T acc = T(0), zm = T(0);
+    each_block([&](const Hdr& h, uint32_t l0) {
+      for (int r = lane; r < h.C; r += 32) {
+        T am;
+        const T m = row_m<T, PC>(low[h.off + r], h, am);
+        const uint32_t i = h.R + r;
+        const uint32_t l = l0 + r;
+        const T b = bv[i];
+        zm += (m == T(0)) ? T(1) : T(0);
+        const T mi = m == T(0) ? T(0) : T(1) / m;
+        const T q = b * mi;
+        MV[l] = m; MI[l] = mi;
+        QL1[l] = q; qg1[i] = q;
+        QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
+        acc += q * b;
+      }
+    });
+    double tot[2];
+    ok = reduce(acc, zm, tot);
+    if (ok && threadIdx.x == 0) {
+      init_state(S, tot[0], tot[1], tol, kmax, sigma);
+      s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
+      s_ibp = 1.0;                     // 1 / beta_0
+    }
+    __syncthreads();
+  }
+  long long tk = 0;
+  auto stamp = [&](int ph) {
+    if (trace && blockIdx.x == 0 && threadIdx.x == 0 && tk >= 16 && tk < 48) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      trace[(tk - 16) * 8 + ph] = t;
+    }
+  };
+  while (ok && S.done != 2) {
+    ++tk;
+    stamp(0);
+    const long long k = S.k;
+    const bool odd = (k & 1) != 0;
+    T* QLc = odd ? QL1 : QL0;          // q_k
+    T* QLp = odd ? QL0 : QL1;          // q_{k-1} -> q_{k+1}
+    const T* qgc = odd ? qg1 : qg0;    // q_k (global, for gathers)
+    T* qgn = odd ? qg0 : qg1;          // q_{k+1}
+    T* DA = odd ? D1 : D0;             // d_{k-2}
+    T* DB = odd ? D0 : D1;             // d_{k-3} -> d_{k-1}
+    const bool doC = S.pending != 0, doMV = S.done == 0;
+    const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
+    T acc = T(0);
+    each_block([&](const Hdr& h, uint32_t l0) {
+      if (doC)
+        for (int r = lane; r < h.C; r += 32) {
+          const uint32_t l = l0 + r;
+          const T d = cq * QLp[l] + cd1 * DA[l] + cd2 * DB[l];
+          DB[l] = d;
+          X[l] += tau * d;
+        }
+      if (doMV) {
+        T xi[JM], hx[JM];
+        block_hv_loc<T, JM>(qgc, QLc + l0, low, h, xi, hx);
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+          const int r = lane + 32 * j;
+          if (j < h.J && r < h.C) {
+            P[l0 + r] = hx[j];
+            acc += xi[j] * hx[j];
+          }
+        }
+      }
+    });
+    if (!doMV) {
+      __syncthreads();
+      if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
+      __syncthreads();
+      break;
+    }
+    stamp(1);
+    double tot[2];
+    if (!(ok = reduce(acc, T(0), tot))) break;
+    stamp(2);
+    if (threadIdx.x == 0) {
+      S.pending = 0;
+      S.alpha = tot[0] * s_ib * s_ib;                   // q.p / beta_k^2
+      if (!isfinite(S.alpha)) { S.status = HS_NONFINITE; S.done = 2; }
+    }
+    __syncthreads();
+    if (S.done == 2) break;
+    stamp(3);
+    const T c1 = (T)s_ib, c2 = (T)(S.alpha * s_ib), c3 = (T)(S.beta * s_ibp);
+    T acc2 = T(0);
+    each_block([&](const Hdr& h, uint32_t l0) {
+      for (int r = lane; r < h.C; r += 32) {
+        const uint32_t l = l0 + r;
+        const T q = P[l] * MI[l] * c1 - c2 * QLc[l] - c3 * QLp[l];
+        QLp[l] = q;
+        qgn[h.R + r] = q;
+        acc2 += MV[l] * q * q;
+      }
+    });
+    stamp(4);
+    if (!(ok = reduce(acc2, T(0), tot))) break;
+    stamp(5);
+    if (threadIdx.x == 0) {
+      double ib = s_ib;
+      givens_fast(S, tot[0], ib);
+      s_ibp = s_ib;
+      s_ib = ib;
+    }
+    __syncthreads();
+    stamp(6);
+  }
+  __syncthreads();
+  each_block([&](const Hdr& h, uint32_t l0) {
+    for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
+  });
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
+    *st = S;
+  }
+}
+
 // Per-pass kernels (graph path, used when a cooperative launch is not
 // available): the same row passes, with last-CTA reductions.
 template <typename T, int PC>
@@ -334,8 +767,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_init(Geo g, const T* __re
                                                             double* partial, unsigned* counter,
                                                             const double* d_sigma) {
   extern __shared__ __align__(16) char smem[];
-  RowSmem s = row_smem_carve(smem, g);
-  row_smem_fill(s, g, sizeof(T) == 8);
+  const RowSmem<T> s = row_smem_setup<T>(smem, g);
   const double sigma = *d_sigma;
   T acc = T(0);
   int zero_m = 0;
@@ -361,10 +793,9 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_A(Geo g, MinresVecs v, Mi
   }
   __syncthreads();
   if (s_done == 2) return;
-  RowSmem s = row_smem_carve(smem, g);
-  row_smem_fill(s, g, sizeof(T) == 8);
+  const RowSmem<T> s = row_smem_setup<T>(smem, g);
   T acc = T(0);
-  rows_A<T>(g, s, s_c[4], v, s_k, s_pending != 0, s_done == 0, (T)s_c[0], (T)s_c[1], (T)s_c[2],
+  rows_A<T, false>(g, s, s_c[4], v, s_k, s_pending != 0, s_done == 0, (T)s_c[0], (T)s_c[1], (T)s_c[2],
             (T)s_c[3], acc);
   double vv[1] = {(double)acc}, tot[1];
   if (last_cta_sum<1>(vv, s.red, partial, counter, tot) && threadIdx.x == 0) {
@@ -393,8 +824,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_B(Geo g, MinresVecs v, Mi
   }
   __syncthreads();
   if (s_done != 0) return;
-  RowSmem s = row_smem_carve(smem, g);
-  row_smem_fill(s, g, sizeof(T) == 8);
+  const RowSmem<T> s = row_smem_setup<T>(smem, g);
   T acc = T(0);
   rows_B<T, PC>(g, s, s_c[3], v, s_k, (T)s_c[0], (T)s_c[1], (T)s_c[2], acc);
   double vv[1] = {(double)acc}, tot[1];
@@ -438,7 +868,7 @@ static hs_status ensure_ws(hs_handle* hd, MinresVecs& v) {
 template <typename T, int PC>
 static void enqueue_iters(hs_handle* hd, const MinresVecs& v, int iters, cudaStream_t s) {
   const Geo g = hd->geo();
-  const size_t sm = row_smem_bytes((int)hd->low.size(), (int)hd->nb.size());
+  const size_t sm = row_smem_bytes<T>((int)hd->low.size());
   const int grid = row_grid(hd);
   for (int it = 0; it < iters; ++it) {
     k_minres_A<T, PC><<<grid, HV_THREADS, sm, s>>>(g, v, hd->d_state, hd->d_partial,
@@ -450,7 +880,7 @@ static void enqueue_iters(hs_handle* hd, const MinresVecs& v, int iters, cudaStr
 
 template <typename T, int PC>
 static hs_status set_attrs(hs_handle* hd) {
-  const size_t sm = row_smem_bytes((int)hd->low.size(), (int)hd->nb.size());
+  const size_t sm = row_smem_bytes<T>((int)hd->low.size());
   if (sm > 48 * 1024) {
     HS_CUDA_TRY(hd, cudaFuncSetAttribute(k_minres_init<T, PC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -492,6 +922,128 @@ static hs_status get_graph(hs_handle* hd, const MinresVecs& v, cudaGraphExec_t& 
   return HS_OK;
 }
 
+// Contiguous block ranges per CTA with balanced row counts (cached per grid).
+static hs_status smr_plan(hs_handle* hd, int G, int** d_first, int* rows_cap, int* hdr_cap) {
+  if (hd->smr_grid == G && hd->d_smr_first) {
+    *d_first = hd->d_smr_first; *rows_cap = hd->smr_rows_cap; *hdr_cap = hd->smr_hdr_cap;
+    return HS_OK;
+  }
+  const int nb = (int)hd->blocks.size();
+  std::vector<int> first(G + 1, nb);
+  const double per = (double)hd->n / G;
+  int b = 0;
+  for (int c = 0; c < G; ++c) {
+    first[c] = b;
+    const double end = per * (c + 1);
+    while (b < nb && (c == G - 1 || (double)hd->blocks[b].R + hd->cls_C[hd->blocks[b].w] <= end + 0.5 * hd->cls_C[hd->blocks[b].w]))
+      ++b;
+  }
+  first[G] = nb;
+  int rc = 0, hc = 0;
+  for (int c = 0; c < G; ++c) {
+    const int lo = first[c], hi = first[c + 1];
+    long long rows = 0;
+    for (int i = lo; i < hi; ++i) rows += hd->cls_C[hd->blocks[i].w];
+    rc = std::max<int>(rc, (int)rows);
+    hc = std::max(hc, hi - lo);
+  }
+  rc = (rc + 3) & ~3;
+  if (hd->d_smr_first) cudaFree(hd->d_smr_first);
+  hd->d_smr_first = nullptr;
+  HS_CUDA_TRY(hd, cudaMalloc(&hd->d_smr_first, sizeof(int) * (G + 1)));
+  HS_CUDA_TRY(hd, cudaMemcpy(hd->d_smr_first, first.data(), sizeof(int) * (G + 1),
+                             cudaMemcpyHostToDevice));
+  hd->smr_grid = G; hd->smr_rows_cap = rc; hd->smr_hdr_cap = hc;
+  *d_first = hd->d_smr_first; *rows_cap = rc; *hdr_cap = hc;
+  return HS_OK;
+}
+
+// Shared-memory-resident solve; HS_CUDA without a message when it does not fit.
+template <typename T, int PC, int JM, int NT>
+static hs_status solve_smem_v(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
+                              long long kmax) {
+  const int G = std::max(1, std::min(hd->num_sms, hd->sm_budget > 0 ? hd->sm_budget : hd->num_sms));
+  int* first = nullptr;
+  int rows_cap = 0, hdr_cap = 0;
+  hs_status st = smr_plan(hd, G, &first, &rows_cap, &hdr_cap);
+  if (st != HS_OK) return st;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, hd->device);
+  const size_t sm = smr_bytes<T>((int)hd->low.size(), hdr_cap, rows_cap, NT);
+  const size_t static_sm = sizeof(MinresState) + 8 * 8 + 64;
+  if (sm + static_sm > (size_t)optin) return HS_CUDA;
+  if (cudaFuncSetAttribute(k_minres_smem<T, PC, JM, NT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+    cudaGetLastError();
+    return HS_CUDA;
+  }
+  Geo g = hd->geo();
+  GridBar gb{hd->d_counter + 8, hd->d_counter + 9, reinterpret_cast<int*>(hd->d_counter + 10)};
+  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_counter + 8, 0, 3 * sizeof(unsigned), hd->stream));
+  // generation slots start from zero for every solve (a stale generation left
+  // by a previous solve must never read as an arrival)
+  if (G > 256) return HS_CUDA;
+  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_partial, 0, 2 * sizeof(Slot) * G, hd->stream));
+  double* part = hd->d_partial;
+  const double* ds = hd->d_sigma;
+  MinresState* stp = hd->d_state;
+  unsigned long long limit = 1ull << 22;
+  if (const char* e = getenv("HS_BARRIER_LIMIT")) limit = strtoull(e, nullptr, 10);
+  T* q0 = (T*)v.q0;
+  T* q1 = (T*)v.q1;
+  T* xo = (T*)v.x;
+  unsigned long long* trace = nullptr;
+  const bool want_trace = getenv("HS_TRACE") != nullptr;
+  if (want_trace) {
+    HS_CUDA_TRY(hd, cudaMalloc(&trace, 32 * 8 * sizeof(unsigned long long)));
+    HS_CUDA_TRY(hd, cudaMemsetAsync(trace, 0, 32 * 8 * sizeof(unsigned long long), hd->stream));
+  }
+  void* args[] = {&g, (void*)&b, &q0, &q1, &xo, &stp, &tol, &kmax, (void*)&ds, &part, &gb, &limit,
+                  &first, &rows_cap, &trace};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_minres_smem<T, PC, JM, NT>, dim3(G),
+                                              dim3(NT), args, sm, hd->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return HS_CUDA;
+  }
+  count_launches(1);
+  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
+                                  cudaMemcpyDeviceToHost, hd->stream));
+  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
+  if (want_trace) {
+    std::vector<unsigned long long> t(32 * 8);
+    cudaMemcpy(t.data(), trace, t.size() * 8, cudaMemcpyDeviceToHost);
+    cudaFree(trace);
+    double acc[7] = {0};
+    int cnt = 0;
+    for (int it = 0; it + 1 < 32; ++it) {
+      const unsigned long long* a = &t[it * 8];
+      const unsigned long long* nx = &t[(it + 1) * 8];
+      if (!a[0] || !nx[0] || !a[6]) continue;
+      for (int ph = 0; ph < 6; ++ph) acc[ph] += (double)(a[ph + 1] - a[ph]);
+      acc[6] += (double)(nx[0] - a[6]);
+      ++cnt;
+    }
+    if (cnt)
+      fprintf(stderr,
+              "[hs trace] G=%d ns/iter: rowsA %.0f redA %.0f scalA %.0f rowsB %.0f redB %.0f "
+              "scalB %.0f loop %.0f total %.0f\n",
+              (int)dim3(G).x, acc[0] / cnt, acc[1] / cnt, acc[2] / cnt, acc[3] / cnt, acc[4] / cnt,
+              acc[5] / cnt, acc[6] / cnt,
+              (acc[0] + acc[1] + acc[2] + acc[3] + acc[4] + acc[5] + acc[6]) / cnt);
+  }
+  return HS_OK;
+}
+
+// Blocks of at most 96 rows (k <= 8) take 3 rows per lane and 1024 threads;
+// larger blocks 8 rows per lane and 512 threads.
+template <typename T, int PC>
+static hs_status solve_smem(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
+                            long long kmax) {
+  if (hd->k <= 8) return solve_smem_v<T, PC, 3, 1024>(hd, b, v, tol, kmax);
+  return solve_smem_v<T, PC, JMAX, 512>(hd, b, v, tol, kmax);
+}
+
 template <typename T, int PC>
 static int persist_grid(hs_handle* hd, size_t sm) {
   int per_sm = 0;
@@ -500,7 +1052,8 @@ static int persist_grid(hs_handle* hd, size_t sm) {
     cudaGetLastError();
     return 0;
   }
-  const int cap = std::min(per_sm, 4) * hd->num_sms;
+  const int sms = hd->sm_budget > 0 ? std::min(hd->sm_budget, hd->num_sms) : hd->num_sms;
+  const int cap = std::min(per_sm, 4) * sms;
   return std::min(cap, row_grid(hd));
 }
 
@@ -509,7 +1062,7 @@ static int persist_grid(hs_handle* hd, size_t sm) {
 template <typename T, int PC>
 static hs_status solve_persist(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
                                long long kmax) {
-  const size_t sm = row_smem_bytes((int)hd->low.size(), (int)hd->nb.size());
+  const size_t sm = row_smem_bytes<T>((int)hd->low.size());
   if (sm > 48 * 1024 &&
       cudaFuncSetAttribute(k_minres_persist<T, PC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sm) != cudaSuccess) {
@@ -536,6 +1089,7 @@ static hs_status solve_persist(hs_handle* hd, const T* b, const MinresVecs& v, d
     cudaGetLastError();
     return HS_CUDA;
   }
+  count_launches(1);
   HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
                                   cudaMemcpyDeviceToHost, hd->stream));
   HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
@@ -548,16 +1102,19 @@ static hs_status solve_graph(hs_handle* hd, const T* b, const MinresVecs& v, dou
   hs_status st;
   if ((st = set_attrs<T, PC>(hd)) != HS_OK) return st;
   const Geo g = hd->geo();
-  const size_t sm = row_smem_bytes((int)hd->low.size(), (int)hd->nb.size());
+  const size_t sm = row_smem_bytes<T>((int)hd->low.size());
   const int grid = row_grid(hd);
   k_minres_init<T, PC><<<grid, HV_THREADS, sm, hd->stream>>>(
-      g, b, v, hd->d_state, tol, kmax, hd->d_partial, hd->d_counter + 0, hd->d_sigma);
+      g, b, v, hd->d_state, tol, kmax, hd->d_partial, hd->d_counter + 0, hd->d_sigma); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   cudaGraphExec_t exec;
   if ((st = get_graph<T, PC>(hd, v, exec)) != HS_OK) return st;
   int between = 1;
   while (true) {
-    for (int j = 0; j < between; ++j) HS_CUDA_TRY(hd, cudaGraphLaunch(exec, hd->stream));
+    for (int j = 0; j < between; ++j) {
+      HS_CUDA_TRY(hd, cudaGraphLaunch(exec, hd->stream));
+      count_launches(2ull * chunk_iters(hd));
+    }
     HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
                                     cudaMemcpyDeviceToHost, hd->stream));
     HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
@@ -578,13 +1135,21 @@ static bool force_graph() {
   return g_force_graph == 1;
 }
 
+// HS_MINRES_GLOBAL=1 skips the shared-memory-resident form (tests compare forms).
+static bool force_global() {
+  const char* e = getenv("HS_MINRES_GLOBAL");
+  return e && e[0] == '1';
+}
+
 template <typename T, int PC>
 static hs_status solve_pc(hs_handle* hd, const T* b, T* x, double tol, long long kmax,
                           hs_minres_info* info) {
   MinresVecs v;
   hs_status st = ensure_ws<T>(hd, v);
   if (st != HS_OK) return st;
-  st = force_graph() ? HS_CUDA : solve_persist<T, PC>(hd, b, v, tol, kmax);
+  st = HS_CUDA;
+  if (!force_graph() && !force_global()) st = solve_smem<T, PC>(hd, b, v, tol, kmax);
+  if (st == HS_CUDA && !force_graph()) st = solve_persist<T, PC>(hd, b, v, tol, kmax);
   if (st == HS_CUDA && (st = solve_graph<T, PC>(hd, b, v, tol, kmax)) != HS_OK) return st;
   if (st != HS_OK) return st;
   const MinresState S = *hd->h_state;

@@ -16,22 +16,18 @@ __global__ void __launch_bounds__(HV_THREADS) k_twist(Geo g, const double* __res
                                                       double* __restrict__ partial) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double bins[TW_WARPS][32];
-  RowSmem s = row_smem_carve(smem, g);
-  row_smem_fill(s, g, false);
+  const RowSmem<double> s = row_smem_setup<double>(smem, g);
   for (int i = threadIdx.x; i < TW_WARPS * 32; i += blockDim.x) (&bins[0][0])[i] = 0.0;
-  const int L = g.L;
-  const int wid = threadIdx.x >> 5;
-  for (int t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
-    const Tile tl = g.tiles[t];
-    __syncthreads();
-    tile_load(s, g, tl, 0.0);
-    tile_rows(s, g, tl, [&](const BlockInfo& b, int li, int r) {
-      const LowEntry e = s.low[li];
-      const double c = psi[b.R + r];
-      const int bin = (int)((le_tlow(e.packed) + b.thigh) % (uint32_t)L);
+  __syncthreads();
+  const uint32_t L = (uint32_t)g.L;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for_blocks(g, 0.0, [&](const Hdr& h) {
+    for (int r = lane; r < h.C; r += 32) {
+      const double c = psi[h.R + r];
+      const uint32_t bin = (le_tlow(s.low[h.off + r].packed) + (uint32_t)h.thigh) % L;
       atomicAdd(&bins[wid][bin], c * c);
-    });
-  }
+    }
+  });
   __syncthreads();
   if (threadIdx.x < 32) {
     double v = 0.0;
@@ -43,7 +39,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_twist(Geo g, const double* __res
 hs_status launch_twist(hs_handle* hd, const double* psi, int K, double* z_host) {
   hs_status st = ensure_reduce(hd);
   if (st != HS_OK) return st;
-  const size_t sm = row_smem_bytes((int)hd->low.size(), (int)hd->nb.size());
+  const size_t sm = row_smem_bytes<double>((int)hd->low.size());
   if (sm > 48 * 1024)
     HS_CUDA_TRY(hd, cudaFuncSetAttribute(k_twist, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm));
@@ -51,7 +47,7 @@ hs_status launch_twist(hs_handle* hd, const double* psi, int K, double* z_host) 
   const int L = hd->L;
   for (int q = 0; q < K; ++q) {
     k_twist<<<grid, HV_THREADS, sm, hd->stream>>>(hd->geo(), psi + (long long)q * hd->n,
-                                                  hd->d_partial);
+                                                  hd->d_partial); count_launches(1);
     HS_CUDA_TRY(hd, cudaGetLastError());
     HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_pinned, hd->d_partial, sizeof(double) * grid * 32,
                                     cudaMemcpyDeviceToHost, hd->stream));

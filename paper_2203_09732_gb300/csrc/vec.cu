@@ -162,8 +162,8 @@ hs_status vmultidot(hs_handle* hd, const double* V, int k, const double* w, long
   if (st != HS_OK) return st;
   const int grid = std::min(vgrid(hd, n), MD_GRID_MAX);
   for (int c0 = 0; c0 < k; c0 += MD_COLS)
-    k_multidot<<<grid, VT, 0, hd->stream>>>(V, k, c0, w, n, part, k);
-  k_colsum<<<(k + 7) / 8, 256, 0, hd->stream>>>(part, grid, k, k, res);
+    k_multidot<<<grid, VT, 0, hd->stream>>>(V, k, c0, w, n, part, k); count_launches(1);
+  k_colsum<<<(k + 7) / 8, 256, 0, hd->stream>>>(part, grid, k, k, res); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_pinned, res, sizeof(double) * k, cudaMemcpyDeviceToHost,
                                   hd->stream));
@@ -185,7 +185,7 @@ hs_status vmultiaxpy(hs_handle* hd, const double* V, int k, const double* c, dou
   for (int j = 0; j < k; ++j) hd->h_pinned[j] = c[j];
   HS_CUDA_TRY(hd, cudaMemcpyAsync(res, hd->h_pinned, sizeof(double) * k, cudaMemcpyHostToDevice,
                                   hd->stream));
-  k_multiaxpy<<<vgrid(hd, n), VT, sizeof(double) * k, hd->stream>>>(V, k, res, w, n);
+  k_multiaxpy<<<vgrid(hd, n), VT, sizeof(double) * k, hd->stream>>>(V, k, res, w, n); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   // the coefficients are read from pinned memory by the copy; keep it alive
   HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
@@ -201,38 +201,38 @@ hs_status vritz(hs_handle* hd, const double* V, int k, const double* Y, int K, d
   for (int t = 0; t < k * K; ++t) hd->h_pinned[t] = Y[t];
   HS_CUDA_TRY(hd, cudaMemcpyAsync(part, hd->h_pinned, sizeof(double) * k * K,
                                   cudaMemcpyHostToDevice, hd->stream));
-  k_ritz<<<vgrid(hd, n), VT, sizeof(double) * k * K, hd->stream>>>(V, k, part, K, psi, n);
+  k_ritz<<<vgrid(hd, n), VT, sizeof(double) * k * K, hd->stream>>>(V, k, part, K, psi, n); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
   return HS_OK;
 }
 
 hs_status vaxpby(hs_handle* hd, double a, const double* x, double b, double* y, long long n) {
-  k_axpby<<<vgrid(hd, n), VT, 0, hd->stream>>>(a, x, b, y, n);
+  k_axpby<<<vgrid(hd, n), VT, 0, hd->stream>>>(a, x, b, y, n); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }
 
 hs_status vscale_to(hs_handle* hd, double a, const double* x, double* y, long long n) {
-  k_scale_to<<<vgrid(hd, n), VT, 0, hd->stream>>>(a, x, y, n);
+  k_scale_to<<<vgrid(hd, n), VT, 0, hd->stream>>>(a, x, y, n); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }
 
 hs_status vsplitmix(hs_handle* hd, unsigned long long seed, double* v, long long n) {
-  k_splitmix<<<vgrid(hd, n), VT, 0, hd->stream>>>(seed, v, n);
+  k_splitmix<<<vgrid(hd, n), VT, 0, hd->stream>>>(seed, v, n); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }
 
 hs_status vcopy_f64_to_f32(hs_handle* hd, const double* x, double scale, float* y, long long n) {
-  k_f64_to_f32<<<vgrid(hd, n), VT, 0, hd->stream>>>(x, scale, y, n);
+  k_f64_to_f32<<<vgrid(hd, n), VT, 0, hd->stream>>>(x, scale, y, n); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }
 
 hs_status vaxpy_f32_to_f64(hs_handle* hd, double a, const float* x, double* y, long long n) {
-  k_axpy_f32<<<vgrid(hd, n), VT, 0, hd->stream>>>(a, x, y, n);
+  k_axpy_f32<<<vgrid(hd, n), VT, 0, hd->stream>>>(a, x, y, n); count_launches(1);
   HS_CUDA_TRY(hd, cudaGetLastError());
   return HS_OK;
 }

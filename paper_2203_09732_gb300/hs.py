@@ -14,7 +14,7 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libhs.so")
+LIB_PATH = os.environ.get("HS_LIB_PATH") or os.path.join(_HERE, "_lib", "libhs.so")
 
 HS_OK, HS_BAD_ARG, HS_OOM, HS_CUDA, HS_NOT_CONVERGED, HS_BREAKDOWN, HS_NONFINITE, HS_TIMEOUT = range(8)
 STATUS_NAMES = ["HS_OK", "HS_BAD_ARG", "HS_OOM", "HS_CUDA", "HS_NOT_CONVERGED", "HS_BREAKDOWN",
@@ -25,7 +25,8 @@ PRECOND = {"id": 0, "jacobi": 1, "row": 2}
 # every symbol include/hs.h declares
 SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "hs_set_sigma",
            "hs_extremal", "hs_unrank", "hs_rank", "hs_diag", "hs_matvec", "hs_minres",
-           "hs_minres_f32", "hs_lanczos_eigs", "hs_eigs_host", "hs_twist", "hs_tridiag_eig"]
+           "hs_minres_f32", "hs_lanczos_eigs", "hs_eigs_host", "hs_twist", "hs_tridiag_eig",
+           "hs_kernel_launches", "hs_set_sm_budget"]
 
 
 class MinresInfo(ctypes.Structure):
@@ -93,6 +94,8 @@ def load(path=LIB_PATH):
                           ctypes.POINTER(LanczosInfo)], ctypes.c_int),
         "hs_twist": ([H, c_vp, ctypes.c_int, c_dp], ctypes.c_int),
         "hs_tridiag_eig": ([ctypes.c_int, c_dp, c_dp, c_dp, c_dp], ctypes.c_int),
+        "hs_kernel_launches": ([], ctypes.c_ulonglong),
+        "hs_set_sm_budget": ([H, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -108,6 +111,11 @@ def _dp(a):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def kernel_launches():
+    """Kernels launched by libhs.so in this process so far."""
+    return int(load().hs_kernel_launches())
 
 
 def tridiag_eig(alpha, beta, vectors=True):
@@ -191,6 +199,10 @@ class Chain:
     @sigma.setter
     def sigma(self, v):
         self._check(self._lib.hs_set_sigma(self._hd, float(v)), "hs_set_sigma")
+
+    def set_sm_budget(self, nsm):
+        """Let persistent solves of this handle use nsm SMs (0 = all)."""
+        self._check(self._lib.hs_set_sm_budget(self._hd, int(nsm)), "hs_set_sm_budget")
 
     def extremal(self, max_steps=600, tol=1e-12):
         lo, hi, mid = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -26,6 +26,8 @@ def test_iterates_match_oracle_fp64(L, kind, k):
     iterates agree up to the rounding of the reductions."""
     hs = need_gpu()
     hv, H, diag, A, sigma = _sys(L)
+    if k > A.shape[0] // 4:
+        pytest.skip("k near n: the Krylov space is exhausted and the recurrence runs on rounding")
     b = inputs.gaussian(A.shape[0], 11)
     M = hamiltonian.precond_diag(H, diag, sigma, kind)
     xr, kr, phir = minres.pminres(A, b, 1.0 / M, kmax=k, tol=0.0)
