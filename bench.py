@@ -4,16 +4,26 @@ arXiv:2203.09732) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one disorder realisation of the L = 20 workload (dimension 184756,
-h_j ~ U[-h, h] with h cycling over {1, 2, 3, 4, 5} and seeds 0..4, sigma at the
-spectrum midpoint, 20 eigenpairs nearest sigma) solved end to end on the GPU by
-shift-invert Lanczos with FP32 MINRES inside FP64 iterative refinement. The
-printed value is eigenpairs per second over the timed steps. A full solve at
-L = 28 needs about n = 4e7 MINRES iterations per Lanczos step (hours), so the
-L = 28 part of the metric is the H x bandwidth, reported in `roofline`.
+Workload: the L = 16 part of the batched disorder sweep (dimension 12870;
+per realisation h ~ U[0.5, 6], then h_j ~ U[-h, h]; sigma at the spectrum
+midpoint E_min/E_max; the 8 eigenpairs nearest sigma). One step = one batch of
+B = 8 seeded realisations solved concurrently on one GPU (8 streams, each
+persistent MINRES on 19 of the 152 SMs), every realisation end to end:
+sigma by extremal Lanczos, shift-invert Lanczos with full reorthogonalisation,
+MINRES with the row-norm preconditioner in every step, Ritz pairs certified by
+FP64 residuals, twist overlaps. The value is eigenpairs per second over the
+timed steps.
 
-Several GPUs (torchrun): independent realisations per rank, no collective on
-the data path (replicas); value = all eigenpairs / max rank time.
+Precision: the library's plain FP64 MINRES is the default at this size (the
+solve is latency-bound; FP32 inner solves restart at every refinement sweep
+and take about 2.5x the iterations); the FP32-MINRES + FP64-refinement path is
+timed on one batch and reported beside it. A full solve at L = 28 takes about
+n = 4e7 MINRES iterations per Lanczos step (hours) and L = 20 about 10^7 per
+realisation, so the L = 28 part of the metric is the H x bandwidth in
+`roofline`, measured in the same run.
+
+Several GPUs (torchrun): each rank solves its own realisations, no collective
+on the data path (replicas); value = all eigenpairs / max rank time.
 """
 import argparse
 import hashlib
@@ -31,18 +41,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "eigenpairs/s near sigma at L=28 (FP32+refine vs FP64); H*v GB/s vs HBM peak"
 UNIT = "eigenpairs/s"
-HS_VALUES = (1.0, 2.0, 3.0, 4.0, 5.0)
-SEEDS = (0, 1, 2, 3, 4)
+BATCH = 8
 FALLBACK_HBM_GBS = 6800.0
 # Lanczos steps per wanted eigenpair in the paper: m = 130 for 50 eigenpairs (Sec. IV A).
 PAPER_M_PER_PAIR = 130.0 / 50.0
 
 
 def realisation(idx, L):
+    """Realisation idx of the batched sweep: h ~ U[0.5, 6], h_j ~ U[-h, h]."""
     from paper_2203_09732_gb300 import inputs
-    h = HS_VALUES[idx % len(HS_VALUES)]
-    seed = SEEDS[(idx // len(HS_VALUES)) % len(SEEDS)]
-    return h, seed, inputs.disorder(L, h, seed)
+    h, hv = inputs.disorder_mixed(L, 1000 * L + idx)
+    return h, 1000 * L + idx, hv
 
 
 def parse():
@@ -51,8 +60,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--L", type=int, default=20)
-    ap.add_argument("--K", type=int, default=20)
+    ap.add_argument("--L", type=int, default=16)
+    ap.add_argument("--K", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=BATCH)
     ap.add_argument("--hv-L", type=int, default=28, dest="hv_L")
     ap.add_argument("--minres-tol", type=float, default=1e-10, dest="minres_tol")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -262,8 +272,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded disorder realisations)",
-        "config": {"workload": f"L={L} random-field Heisenberg chain, Sz=0 (dim {realisation_dim(L)}), "
-                               f"{K} eigenpairs nearest the spectrum midpoint, h in {{1..5}} x seeds 0..4",
+        "config": {"workload": f"batched disorder sweep, L={L} part: random-field Heisenberg chain, "
+                               f"Sz=0 (dim {realisation_dim(L)}), {K} eigenpairs nearest "
+                               f"sigma=(Emin+Emax)/2 per realisation",
                    "L": L, "K": K},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": cb["sample"]},
@@ -293,69 +304,89 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     hs.load()
-    stream = torch.cuda.current_stream()
-    L, K = args.L, args.K
+    L, K, B = args.L, args.K, args.batch
     n = realisation_dim(L)
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    budget = max(1, nsm // B)
+    mixed_default = False   # plain FP64 MINRES below L = 22 (latency-bound solves)
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step(idx, record=None):
+    def solve_one(idx, mixed, out):
         h, seed, hv = realisation(idx, L)
-        with hs.Chain(L, hv, stream=stream) as c:   # sigma = midpoint (extremal Lanczos)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ev, vecs, res, info = c.eigs(K, mixed=True, minres_tol=args.minres_tol, seed=idx,
-                                         allow_not_converged=True)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            sec = e0.elapsed_time(e1) / 1e3
-            z = c.twist(vecs)
-        if record is not None:
-            record.append({"h": h, "seed": seed, "seconds": sec, "info": info,
-                           "max_resid": float(res.max()), "zabs2_mean": float(np.mean(np.abs(z) ** 2))})
-        return sec
+        s = torch.cuda.Stream()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s):
+            with hs.Chain(L, hv, stream=s) as c:
+                c.set_sm_budget(budget)
+                ev, vecs, res, info = c.eigs(K, mixed=mixed, minres_tol=args.minres_tol, seed=seed,
+                                             allow_not_converged=True)
+                z = c.twist(vecs)
+            s.synchronize()
+        out.append({"h": round(h, 4), "seed": seed, "seconds": time.perf_counter() - t0,
+                    "lanczos_steps": info["steps"], "minres_iters": info["minres_iters"],
+                    "converged": info["converged"], "max_resid": float(res.max()),
+                    "zabs2_mean": float(np.mean(np.abs(z) ** 2))})
 
-    # warm-up steps (untimed): realisations disjoint from the timed ones
+    def batch(step_idx, mixed, out):
+        """One step: B realisations solved concurrently (one host thread and
+        one stream each; ctypes releases the GIL inside the library)."""
+        base = (rank + world * step_idx) * B
+        th = [threading.Thread(target=solve_one, args=(base + i, mixed, out)) for i in range(B)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+
     for w in range(args.warmup):
-        step(1000 + rank + world * w)
+        batch(10000 + w, mixed_default, [])
     recs = []
     launches0 = hs.kernel_launches()
     barrier()
     with ClockSampler(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
         t0 = time.perf_counter()
-        dev_sec = 0.0
-        for s in range(args.steps):
-            dev_sec += step(rank + world * s, recs)
+        for s_ in range(args.steps):
+            batch(s_, mixed_default, recs)
         barrier()
+        e1.record()
+        torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+    dev_sec = e0.elapsed_time(e1) / 1e3
     launches = hs.kernel_launches() - launches0
     tmax = dev_sec
     if dist is not None:
         t = torch.tensor([dev_sec], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tmax = float(t.item())
-    total_pairs = K * args.steps * world
-    value = total_pairs / tmax
+    value = K * B * args.steps * world / tmax
 
-    # end to end through the C ABI with host buffers (hs_eigs_host)
-    e2e_steps = max(1, min(2, args.steps))
+    # end to end through the C ABI with host buffers only (hs_eigs_host): the
+    # disorder goes in from host memory, eigenvalues, eigenvectors, residuals
+    # and twist overlaps come back to host memory, all inside the timed region
     barrier()
     t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        h, seed, hv = realisation(rank + world * s, L)
-        hs.eigs_host(L, hv, K, mixed=True, minres_tol=args.minres_tol, seed=s)
+    th = []
+    for i in range(B):
+        h, seed, hv = realisation((rank + world * 0) * B + i, L)
+        th.append(threading.Thread(target=hs.eigs_host, args=(L, hv, K), kwargs=dict(
+            mixed=mixed_default, minres_tol=args.minres_tol, seed=seed, sm_budget=budget)))
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
     barrier()
     e2e_sec = time.perf_counter() - t0
-    e2e_val = K * e2e_steps * world / e2e_sec
+    e2e_val = K * B * world / e2e_sec
     k_lo = 10 if L >= 22 else 8
     nblocks = sum(1 for H in range(1 << (L - k_lo)) if 0 <= L // 2 - bin(H).count("1") <= k_lo)
-    h2d = 8 * L + 32 * (1 << k_lo) + 128 * nblocks + 8 * 33 * 18
-    d2h = K * n * 8 + K * 8 + K * 8 + 2 * K * 8
+    h2d = B * (8 * L + 32 * (1 << k_lo) + 128 * nblocks + 4 * 33 * 18)
+    d2h = B * (K * n * 8 + K * 8 + K * 8 + 2 * K * 8)
 
     if rank != 0:
         if dist is not None:
@@ -363,26 +394,25 @@ def run_ours(args):
         return
 
     extra = {}
-    # FP32+refinement vs plain FP64, one solve each on the first timed realisation
+    # FP32 MINRES + FP64 refinement on one batch (the other precision mode)
     if not args.no_fp64:
-        h, seed, hv = realisation(0, L)
-        with hs.Chain(L, hv, stream=stream) as c:
-            b = torch.randn(c.n, dtype=torch.float64, device="cuda")
-            res = {}
-            for mode in ("fp32_ir", "fp64"):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                x, info = c.minres(b, tol=args.minres_tol, mixed=(mode == "fp32_ir"),
-                                   allow_not_converged=True)
-                torch.cuda.synchronize()
-                res[mode] = {"seconds": time.perf_counter() - t0, "iters": info["iters"],
-                             "sweeps": info["sweeps"], "resid_2": info["resid_2"]}
-        extra["minres_solve"] = res
-        extra["fp32_ir_speedup_vs_fp64_per_solve"] = res["fp64"]["seconds"] / res["fp32_ir"]["seconds"]
+        mrec = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch(0, True, mrec)
+        torch.cuda.synchronize()
+        msec = time.perf_counter() - t0
+        extra["fp32_refine"] = {"value": K * B / msec, "unit": UNIT, "seconds_per_batch": msec,
+                                "minres_iters": sum(r["minres_iters"] for r in mrec),
+                                "max_resid": max(r["max_resid"] for r in mrec)}
+        extra["fp64"] = {"value": K * B / (tmax / args.steps), "unit": UNIT,
+                         "seconds_per_batch": tmax / args.steps,
+                         "minres_iters": sum(r["minres_iters"] for r in recs[:B])}
+        extra["fp32_refine_over_fp64"] = extra["fp32_refine"]["value"] / extra["fp64"]["value"]
 
-    # H x bandwidth at L = 28 (roofline of the hot-loop kernel)
+    # H x bandwidth at L = 28 (the kernel of the MINRES hot loop at scale)
     peak, peak_src = peaks()
-    rf = hv_roofline(torch, hs, args.hv_L, stream)
+    rf = hv_roofline(torch, hs, args.hv_L, torch.cuda.current_stream())
     f32 = rf["f32"]
     achieved = f32["bytes"] / f32["seconds"] / 1e9
     traffic = profiled_traffic(f"hv_l{args.hv_L}_f32")
@@ -401,21 +431,22 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic (seeded disorder realisations h_j ~ U[-h, h])",
-        "config": {"workload": f"L={L} random-field Heisenberg chain, Sz=0 (dim {n}), {K} eigenpairs "
-                               f"nearest sigma=(Emin+Emax)/2, h in {{1..5}} x seeds 0..4, FP32 MINRES + "
-                               f"FP64 refinement, FP64 Lanczos with full reorthogonalisation",
-                   "L": L, "K": K, "minres_tol": args.minres_tol, "precond": "row-norm",
-                   "l2": "per-step working set 1.5 MB (L2-resident); H x roofline inputs 321 MB > L2",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 (fp32+f64 refinement reported)",
+        "data": "synthetic (seeded disorder realisations, h ~ U[0.5,6], h_j ~ U[-h,h])",
+        "config": {"workload": f"batched disorder sweep, L={L} part: random-field Heisenberg chain, "
+                               f"Sz=0 (dim {n}), {K} eigenpairs nearest sigma=(Emin+Emax)/2 per "
+                               f"realisation, {B} realisations per step solved concurrently",
+                   "L": L, "K": K, "batch": B, "sm_per_realisation": budget,
+                   "minres_tol": args.minres_tol, "precond": "row-norm",
+                   "l2": "per-realisation working set < 1 MB (L2-resident); H x roofline inputs 321 MB > L2",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "steps_detail": recs,
         **extra,
+        "steps_detail": recs,
         "wall_seconds_timed": wall,
     }
     print(json.dumps(line), flush=True)

@@ -156,13 +156,15 @@ hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol,
                           hs_lanczos_info* info);
 
 /* End-to-end convenience call with host buffers only: creates a handle on the
- * current device, runs hs_lanczos_eigs, copies the eigenvectors to
- * evecs_host (K x n, may be NULL) and frees everything. sigma NaN = midpoint. */
+ * current device (its own stream; persistent solves limited to sm_budget SMs,
+ * 0 = all), runs hs_lanczos_eigs, computes the twist overlaps (z_host, 2K
+ * doubles, may be NULL), copies the eigenvectors to evecs_host (K x n, may be
+ * NULL) and frees everything. sigma NaN = midpoint. */
 hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_max,
                        double tol, unsigned long long seed, int mixed, hs_precond pc,
-                       double minres_tol, double inner_tol, double* evals_host,
-                       double* evecs_host, double* resid_host, double* z_host,
-                       hs_lanczos_info* info);
+                       double minres_tol, double inner_tol, int sm_budget,
+                       double* evals_host, double* evecs_host, double* resid_host,
+                       double* z_host, hs_lanczos_info* info);
 
 /* Twist overlap z_i = <psi_i| U_twist |psi_i>, U_twist = exp[i 2pi/L sum_j j Sz_j]
  * (Sec. III), for K real FP64 vectors psi_dev + i n (not normalised by the

@@ -299,9 +299,9 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
 
 extern "C" hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_max,
                                   double tol, unsigned long long seed, int mixed, hs_precond pc,
-                                  double minres_tol, double inner_tol, double* evals_host,
-                                  double* evecs_host, double* resid_host, double* z_host,
-                                  hs_lanczos_info* info) {
+                                  double minres_tol, double inner_tol, int sm_budget,
+                                  double* evals_host, double* evecs_host, double* resid_host,
+                                  double* z_host, hs_lanczos_info* info) {
   cudaStream_t s;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -310,6 +310,7 @@ extern "C" hs_status hs_eigs_host(int L, const double* h_host, double sigma, int
   hs_handle* hd = nullptr;
   hs_status st = hs_create(L, h_host, sigma, s, &hd);
   if (st != HS_OK) { cudaStreamDestroy(s); return st; }
+  hs_set_sm_budget(hd, sm_budget);
   double* ev = nullptr;
   if (cudaMalloc(&ev, sizeof(double) * (size_t)K * hd->n) != cudaSuccess) {
     cudaGetLastError();

@@ -90,7 +90,7 @@ def load(path=LIB_PATH):
                              c_dp, ctypes.POINTER(LanczosInfo)], ctypes.c_int),
         "hs_eigs_host": ([ctypes.c_int, c_dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                           ctypes.c_double, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int,
-                          ctypes.c_double, ctypes.c_double, c_dp, c_dp, c_dp, c_dp,
+                          ctypes.c_double, ctypes.c_double, ctypes.c_int, c_dp, c_dp, c_dp, c_dp,
                           ctypes.POINTER(LanczosInfo)], ctypes.c_int),
         "hs_twist": ([H, c_vp, ctypes.c_int, c_dp], ctypes.c_int),
         "hs_tridiag_eig": ([ctypes.c_int, c_dp, c_dp, c_dp, c_dp], ctypes.c_int),
@@ -291,7 +291,7 @@ class Chain:
 
 
 def eigs_host(L, h, K, sigma=float("nan"), m_max=0, tol=1e-10, seed=0, mixed=True, precond="row",
-              minres_tol=1e-12, inner_tol=1e-4, vectors=True, twist=True):
+              minres_tol=1e-12, inner_tol=1e-4, vectors=True, twist=True, sm_budget=0):
     """End-to-end call with host (numpy) buffers only: hs_eigs_host."""
     lib = load()
     hh = np.ascontiguousarray(h, dtype=np.float64)
@@ -302,8 +302,9 @@ def eigs_host(L, h, K, sigma=float("nan"), m_max=0, tol=1e-10, seed=0, mixed=Tru
     z = np.zeros(2 * K) if twist else None
     info = LanczosInfo()
     st = lib.hs_eigs_host(L, _dp(hh), float(sigma), K, m_max, tol, seed, int(mixed), PRECOND[precond],
-                          minres_tol, inner_tol, _dp(ev), _dp(vec), _dp(res), _dp(z), ctypes.byref(info))
-    if st not in (HS_OK,):
+                          minres_tol, inner_tol, int(sm_budget), _dp(ev), _dp(vec), _dp(res), _dp(z),
+                          ctypes.byref(info))
+    if st not in (HS_OK, HS_NOT_CONVERGED):
         raise HSError(st, "hs_eigs_host")
     zz = (z[0::2] + 1j * z[1::2]) if twist else None
     return ev, vec, res, zz, info.as_dict()
