@@ -171,6 +171,26 @@ hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_m
  * call). z_host[2 i] = Re z_i, z_host[2 i + 1] = Im z_i. */
 hs_status hs_twist(hs_handle* hd, const double* psi_dev, int K, double* z_host);
 
+/* Twist overlaps without any device allocation, for callers that cannot call
+ * cudaMalloc (code inside someone else's stream capture, plug-ins whose host
+ * application owns every device allocation, processes that already hold
+ * nearly all device memory). The paper has no counterpart; it computes the
+ * same z_i as hs_twist, with no handle.
+ *   L: even, 4 <= L <= 32; psi_dev: K FP64 vectors of n = C(L, L/2) entries in
+ *   rank order (vector i at psi_dev + i n); 1 <= K <= 8 (the fixed scratch holds
+ *   8 vectors; larger K returns HS_BAD_ARG); z_dev: 2K doubles on the device,
+ *   z_dev[2i] = Re z_i, z_dev[2i+1] = Im z_i; cuda_stream: where the work is
+ *   enqueued (asynchronous, nothing is synchronised).
+ * Scratch: a fixed 512 KiB static device array inside this library (held by
+ * every GPU that loads it until the process exits); no cudaMalloc, cudaFree
+ * or allocating library routine is called. The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. Every call shares
+ * the array and its arrival counter: calls whose work overlaps on the GPU (for
+ * example on two streams at once) race and must be serialised by the caller. */
+hs_status hs_twist_noalloc(int L, const double* psi_dev, int K, double* z_dev,
+                           void* cuda_stream);
+
 /* Host-only: eigen-decomposition of the symmetric tridiagonal T (diagonal
  * alpha[0..k), off-diagonal beta[0..k-1)) by implicit QL with Wilkinson shifts.
  * theta[k] ascending; Y (k x k, column-major, may be NULL) eigenvectors.

@@ -26,7 +26,7 @@ PRECOND = {"id": 0, "jacobi": 1, "row": 2}
 SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "hs_set_sigma",
            "hs_extremal", "hs_unrank", "hs_rank", "hs_diag", "hs_matvec", "hs_minres",
            "hs_minres_f32", "hs_lanczos_eigs", "hs_eigs_host", "hs_twist", "hs_tridiag_eig",
-           "hs_kernel_launches", "hs_set_sm_budget"]
+           "hs_kernel_launches", "hs_set_sm_budget", "hs_twist_noalloc"]
 
 
 class MinresInfo(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(path=LIB_PATH):
         "hs_tridiag_eig": ([ctypes.c_int, c_dp, c_dp, c_dp, c_dp], ctypes.c_int),
         "hs_kernel_launches": ([], ctypes.c_ulonglong),
         "hs_set_sm_budget": ([H, ctypes.c_int], ctypes.c_int),
+        "hs_twist_noalloc": ([ctypes.c_int, c_vp, ctypes.c_int, c_vp, c_vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -111,6 +112,17 @@ def _dp(a):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def twist_noalloc(L, psi, z, stream=None):
+    """hs_twist_noalloc: twist overlaps of the K rows of psi (CUDA float64,
+    K x n) into z (CUDA float64, 2K), with no device allocation. Returns the
+    status code; asynchronous on `stream` (default: the current stream)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    K = psi.shape[0] if psi.dim() == 2 else 1
+    return int(load().hs_twist_noalloc(int(L), _ptr(psi), int(K), _ptr(z),
+                                       ctypes.c_void_p(s.cuda_stream)))
 
 
 def kernel_launches():
