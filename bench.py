@@ -54,6 +54,13 @@ def realisation(idx, L):
     return h, 1000 * L + idx, hv
 
 
+def rank_realisations(rank, world, step, batch):
+    """Realisation indices of one step on one rank: disjoint across ranks and
+    steps (replicas, weak scaling)."""
+    base = (rank + world * step) * batch
+    return [base + i for i in range(batch)]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -67,6 +74,10 @@ def parse():
     ap.add_argument("--minres-tol", type=float, default=1e-10, dest="minres_tol")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--only", choices=["hv", "minres"], default=None,
+                    help="profiling cases: only the H x timing (--hv-L), or one FP64 MINRES "
+                         "solve of --minres-iters iterations at --L")
+    ap.add_argument("--minres-iters", type=int, default=2000, dest="minres_iters")
     return ap.parse_args()
 
 
@@ -334,8 +345,8 @@ def run_ours(args):
     def batch(step_idx, mixed, out):
         """One step: B realisations solved concurrently (one host thread and
         one stream each; ctypes releases the GIL inside the library)."""
-        base = (rank + world * step_idx) * B
-        th = [threading.Thread(target=solve_one, args=(base + i, mixed, out)) for i in range(B)]
+        th = [threading.Thread(target=solve_one, args=(idx, mixed, out))
+              for idx in rank_realisations(rank, world, step_idx, B)]
         for t in th:
             t.start()
         for t in th:
@@ -372,8 +383,8 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     th = []
-    for i in range(B):
-        h, seed, hv = realisation((rank + world * 0) * B + i, L)
+    for idx in rank_realisations(rank, world, 0, B):
+        h, seed, hv = realisation(idx, L)
         th.append(threading.Thread(target=hs.eigs_host, args=(L, hv, K), kwargs=dict(
             mixed=mixed_default, minres_tol=args.minres_tol, seed=seed, sm_budget=budget)))
     for t in th:
@@ -424,6 +435,20 @@ def run_ours(args):
                 "f64": {"achieved": rf["f64"]["bytes"] / rf["f64"]["seconds"] / 1e9,
                         "launch_us": rf["f64"]["seconds"] * 1e6}}
 
+    # the dominant kernel of the timed step: the persistent MINRES solve
+    # (99.95 % of GPU time in the launch list); its problem lives on chip, so
+    # its HBM fraction is small by construction
+    iters = sum(r["minres_iters"] for r in recs)
+    alg = 12.0 * n * 8 * iters
+    dominant = {"kernel": "k_minres_smem<double, row-norm> (persistent MINRES, one launch per solve)",
+                "bound": "latency (L2/shared-memory resident; two grid reductions per iteration)",
+                "minres_iterations_timed": iters,
+                "algorithmic_bytes_per_iteration": 12.0 * n * 8,
+                "achieved_GBps_all_streams": alg / tmax / 1e9,
+                "frac_of_hbm_peak": alg / tmax / 1e9 / peak,
+                "us_per_iteration_per_realisation": float(np.mean(
+                    [r["seconds"] / max(1, r["minres_iters"]) * 1e6 for r in recs]))}
+
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(L, K)
@@ -443,6 +468,7 @@ def run_ours(args):
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roofline,
+        "dominant_kernel": dominant,
         "cpu_baseline": cpu,
         "clocks": clocks,
         **extra,
@@ -454,9 +480,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_only(args):
+    """Single-kernel cases for profiler captures."""
+    import torch
+
+    from paper_2203_09732_gb300 import hs
+    torch.cuda.set_device(0)
+    if args.only == "hv":
+        rf = hv_roofline(torch, hs, args.hv_L, torch.cuda.current_stream())
+        print(json.dumps({k: {"GB/s": v["bytes"] / v["seconds"] / 1e9, "us": v["seconds"] * 1e6}
+                          for k, v in rf.items()}))
+        return
+    h, seed, hv = realisation(0, args.L)
+    with hs.Chain(args.L, hv) as c:
+        b = torch.randn(c.n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, info = c.minres(b, tol=0.0, kmax=args.minres_iters, allow_not_converged=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    print(json.dumps({"L": args.L, "iters": info["iters"], "us_per_iter": dt / info["iters"] * 1e6}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
