@@ -165,6 +165,9 @@ hs_status fail(hs_handle* hd, hs_status st, const std::string& msg);
 
 // launchers implemented in hv.cu -------------------------------------------
 hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted);
+// hv_tma.cu: staged form for blocks of up to 252 rows; *used = false if it does not apply
+hs_status launch_matvec_tma(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted,
+                            bool* used);
 hs_status launch_unrank(hs_handle* hd, long long first, long long count, unsigned int* out);
 hs_status launch_rank(hs_handle* hd, const unsigned int* st, long long count, long long* out);
 hs_status launch_diag(hs_handle* hd, double* diag, hs_precond pc, double* minv);

@@ -1,6 +1,8 @@
 // Matrix-free H x (Eq. (1)), the basis ranking (Sec. I: Sz = 0 sector in
 // ascending integer order), the diagonal / preconditioner export (Sec. II) and
 // the FP64 refinement residual r = b - (H - sigma) x.
+#include <cstdlib>
+
 #include "rows.cuh"
 
 namespace hs {
@@ -145,6 +147,13 @@ static hs_status prep_smem(hs_handle* hd, K kern, size_t bytes) {
 }
 
 hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted) {
+  if (const char* e = getenv("HS_HV_TMA")) {
+    if (e[0] == '1') {
+      bool used = false;
+      hs_status st = launch_matvec_tma(hd, x, y, dt, shifted, &used);
+      if (st != HS_OK || used) return st;
+    }
+  }
   const Geo g = hd->geo();
   const int grid = row_grid(hd);
   if (dt == HS_F32) {

@@ -1404,7 +1404,10 @@ static hs_status solve_cluster(hs_handle* hd, const T* b, const MinresVecs& v, d
 template <typename T, int PC>
 static hs_status solve_smem(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
                             long long kmax) {
-  if (hd->k <= 8) return solve_smem_v<T, PC, 3, 1024>(hd, b, v, tol, kmax);
+  // FP64 rows need more than the 64 registers a 1024-thread CTA allows
+  if (hd->k <= 8)
+    return sizeof(T) == 8 ? solve_smem_v<T, PC, 3, 512>(hd, b, v, tol, kmax)
+                          : solve_smem_v<T, PC, 3, 1024>(hd, b, v, tol, kmax);
   return solve_smem_v<T, PC, JMAX, 512>(hd, b, v, tol, kmax);
 }
 
