@@ -1,0 +1,95 @@
+"""More GPU parity for rows a1 and a6-a9: larger chains against dense
+eigh, the FP32+refinement eigensolve, edge cases of the Lanczos driver, and
+full-size ranking samples against the oracle's counting rank."""
+import numpy as np
+import pytest
+
+from oracle import basis, hamiltonian, twist
+from paper_2203_09732_gb300 import inputs
+from tests.gpu_util import need_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def l14():
+    L = 14
+    hv = inputs.disorder(L, 2.5, 11)
+    H, diag, st = hamiltonian.build(L, hv)
+    w, V = np.linalg.eigh(H.toarray())
+    return L, hv, H, st, w, V
+
+
+@pytest.mark.parametrize("mixed,tol", [(False, 1e-10), (True, 1e-9)])
+def test_l14_eigs_and_twist_vs_dense(l14, mixed, tol):
+    hs = need_gpu()
+    L, hv, H, st, w, V = l14
+    sigma = 0.5 * (w[0] + w[-1])
+    K = 12
+    idx = np.lexsort((w, np.abs(w - sigma)))[:K]
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        ev, vecs, res, info = c.eigs(K, mixed=mixed, seed=5)
+        z = c.twist(vecs)
+    assert np.abs(ev - w[idx]).max() < tol
+    assert res.max() < 1e-8 and info["converged"] == K
+    zr = twist.overlap(V[:, idx], st, L)
+    assert np.abs(np.abs(z) ** 2 - np.abs(zr) ** 2).max() < 1e-8
+
+
+def test_single_pair_and_step_cap(l14):
+    hs = need_gpu()
+    L, hv, H, st, w, V = l14
+    sigma = 0.5 * (w[0] + w[-1])
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        ev, vecs, res, info = c.eigs(1, seed=2)
+        near = w[np.argmin(np.abs(w - sigma))]
+        assert abs(ev[0] - near) < 1e-10
+        # a step cap below what convergence needs reports HS_NOT_CONVERGED
+        with pytest.raises(hs.HSError) as e:
+            c.eigs(6, m_max=6, seed=2)
+        assert e.value.status == hs.HS_NOT_CONVERGED
+        ev2, _, _, info2 = c.eigs(6, m_max=6, seed=2, allow_not_converged=True)
+        assert info2["steps"] == 6 and info2["converged"] < 6
+
+
+def test_sm_budget_gives_same_answer(l14):
+    hs = need_gpu()
+    L, hv, H, st, w, V = l14
+    sigma = 0.5 * (w[0] + w[-1])
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        e_all, _, _, _ = c.eigs(4, seed=3, vectors=False)
+        c.set_sm_budget(7)
+        e_few, _, _, _ = c.eigs(4, seed=3, vectors=False)
+    assert np.abs(e_all - e_few).max() < 1e-10
+
+
+@pytest.mark.parametrize("L", [26, 28])
+def test_full_size_ranking_samples(L):
+    """Bit-exact unrank/rank at full size against the oracle's counting rank."""
+    hs = need_gpu()
+    rng = np.random.default_rng(L)
+    n = inputs.dim(L)
+    with hs.Chain(L, np.zeros(L), sigma=0.0) as c:
+        firsts = np.concatenate([[0, n - 1000], rng.integers(0, n - 1000, 6)])
+        for f in firsts:
+            s = c.unrank(int(f), 1000).cpu().numpy().astype(np.int64) & 0xFFFFFFFF
+            for j in range(0, 1000, 97):
+                assert s[j] == basis.unrank_count(int(f) + j, L)
+            assert (np.diff(s) > 0).all()
+            r = c.rank(torch.from_numpy(s.astype(np.uint32).view(np.int32)).cuda()).cpu().numpy()
+            assert (r == np.arange(f, f + 1000)).all()
+
+
+def test_host_buffers_end_to_end_with_budget():
+    hs = need_gpu()
+    L = 12
+    hv = inputs.disorder(L, 3.0, 0)
+    H, diag, st = hamiltonian.build(L, hv)
+    w, V = np.linalg.eigh(H.toarray())
+    sigma = 0.5 * (w[0] + w[-1])
+    idx = np.lexsort((w, np.abs(w - sigma)))[:5]
+    ev, vec, res, z, info = hs.eigs_host(L, hv, 5, mixed=False, sm_budget=4)
+    assert np.abs(ev - w[idx]).max() < 1e-10
+    ov = np.abs(np.einsum("in,ni->i", vec, V[:, idx]))
+    assert (ov > 1 - 1e-8).all()
+    assert np.abs(np.abs(z) ** 2 - np.abs(twist.overlap(V[:, idx], st, L)) ** 2).max() < 1e-8

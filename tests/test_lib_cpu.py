@@ -65,3 +65,17 @@ def test_create_rejects_bad_arguments_without_gpu(lib):
     st = lib.hs_create(4, hn.ctypes.data_as(hs.c_dp), 0.0, None, ctypes.byref(hd))
     assert st == hs.HS_BAD_ARG
     assert lib.hs_last_error(None) == b"null handle"
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    """No CPU fallback: a missing libhs.so is an error, not a silent path."""
+    import importlib
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import os; os.environ['HS_LIB_PATH'] = %r\n"
+            "from paper_2203_09732_gb300 import hs\n"
+            "try:\n    hs.load()\nexcept RuntimeError as e:\n    print('raised', e)\n") % (
+        ROOT, str(tmp_path / "missing.so"))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert "raised" in r.stdout and "missing" in r.stdout
