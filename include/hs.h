@@ -125,7 +125,7 @@ hs_status hs_matvec(hs_handle* hd, const void* x_dev, void* y_dev, hs_dtype dtyp
  *   mixed = 1: FP32 MINRES (FP32 vectors and H x, FP64 scalar recurrences)
  *              inside FP64 iterative refinement of the residual
  *              r = b - (H - sigma) x, until ||r||_{M^-1} <= tol ||b||_{M^-1}
- *              (each sweep runs to the relative tolerance inner_tol).
+ *              (each sweep runs to the relative tolerance inner_tol; <= 0: 1e-5).
  * b_dev and x_dev are FP64, n elements, may not overlap. info may be NULL.
  * Returns HS_NOT_CONVERGED (x still holds the last iterate) if the cap is hit. */
 hs_status hs_minres(hs_handle* hd, const double* b_dev, double* x_dev, double tol,

@@ -373,7 +373,7 @@ hs_status hs_minres(hs_handle* hd, const double* b_dev, double* x_dev, double to
     }
     return st;
   }
-  const double itol = inner_tol > 0 ? inner_tol : 1e-4;
+  const double itol = inner_tol > 0 ? inner_tol : 1e-5;
   return minres_mixed(hd, b_dev, x_dev, tol, kmax, pc, itol, info);
 }
 

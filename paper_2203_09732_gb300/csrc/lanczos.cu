@@ -201,7 +201,7 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
     double* vk = V + (size_t)k * n;
     const auto ts = clk::now();
     std::memset(&mi, 0, sizeof(mi));
-    if (mixed) st = minres_mixed(hd, vk, x, minres_tol, 50 * n, pc, inner_tol > 0 ? inner_tol : 1e-4, &mi);
+    if (mixed) st = minres_mixed(hd, vk, x, minres_tol, 50 * n, pc, inner_tol > 0 ? inner_tol : 1e-5, &mi);
     else st = minres_solve64(hd, vk, x, minres_tol, 50 * n, pc, &mi);
     solve_s += std::chrono::duration<double>(clk::now() - ts).count();
     if (info) { info->minres_iters += mi.iters; info->sweeps += mixed ? mi.sweeps : 1; }

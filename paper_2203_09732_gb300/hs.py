@@ -252,7 +252,7 @@ class Chain:
         self._check(self._lib.hs_matvec(self._hd, _ptr(x), _ptr(y), dt, int(shifted)), "hs_matvec")
         return y
 
-    def minres(self, b, x=None, tol=1e-12, kmax=0, precond="row", mixed=False, inner_tol=1e-4,
+    def minres(self, b, x=None, tol=1e-12, kmax=0, precond="row", mixed=False, inner_tol=1e-5,
                allow_not_converged=False):
         t = self.torch
         self._vec(b, t.float64)
@@ -278,7 +278,7 @@ class Chain:
         return x, info.as_dict()
 
     def eigs(self, K, m_max=0, tol=1e-10, seed=0, v0=None, mixed=False, precond="row",
-             minres_tol=1e-12, inner_tol=1e-4, vectors=True, allow_not_converged=False):
+             minres_tol=1e-12, inner_tol=1e-5, vectors=True, allow_not_converged=False):
         t = self.torch
         ev = np.zeros(K)
         res = np.zeros(K)
@@ -303,7 +303,7 @@ class Chain:
 
 
 def eigs_host(L, h, K, sigma=float("nan"), m_max=0, tol=1e-10, seed=0, mixed=True, precond="row",
-              minres_tol=1e-12, inner_tol=1e-4, vectors=True, twist=True, sm_budget=0):
+              minres_tol=1e-12, inner_tol=1e-5, vectors=True, twist=True, sm_budget=0):
     """End-to-end call with host (numpy) buffers only: hs_eigs_host."""
     lib = load()
     hh = np.ascontiguousarray(h, dtype=np.float64)
