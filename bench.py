@@ -145,7 +145,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("rows.cuh", "hv.cu", "common.cuh"):
+    for f in ("rows.cuh", "hv.cu", "common.cuh", "sb.cuh", "hv_sb.cu"):
         h.update(open(os.path.join(ROOT, "paper_2203_09732_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -169,6 +169,14 @@ def profiled_traffic(name):
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def hv_kernel_name(L):
+    """The H x kernel hs_matvec launches at L in FP32: the superblock form
+    from L = 24 on (unless HS_HV_SB=0), the block form below."""
+    e = os.environ.get("HS_HV_SB")
+    on = (e == "1" and L >= 22) if e is not None else L >= 24
+    return "k_matvec_sb<float>" if on else "k_matvec<float>"
 
 
 def hv_roofline(torch, hs, L, stream):
@@ -429,7 +437,7 @@ def run_ours(args):
     traffic = profiled_traffic(f"hv_l{args.hv_L}_f32")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"k_matvec<float> (H - sigma) x at L={args.hv_L}, n={f32['n']}",
+                "kernel": f"{hv_kernel_name(args.hv_L)} (H - sigma) x at L={args.hv_L}, n={f32['n']}",
                 "algorithmic_bytes_per_launch": f32["bytes"],
                 "launch_us": f32["seconds"] * 1e6, "peak_source": peak_src,
                 "f64": {"achieved": rf["f64"]["bytes"] / rf["f64"]["seconds"] / 1e9,

@@ -254,6 +254,7 @@ hs_status hs_create(int L, const double* h_host, double sigma, void* cuda_stream
       for (int c = 0; c < W; ++c) bt[a * W + c] = binom(a, c);
     if ((st = upload(hd, &hd->d_binom, bt)) != HS_OK) return bail(st);
   }
+  if (L >= 22 && (st = sb_setup(hd)) != HS_OK) return bail(st);
   if (cudaMalloc(&hd->d_sigma, sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(HS_OOM); }
   if ((st = ensure_reduce(hd)) != HS_OK) return bail(st);
   if (std::isnan(sigma)) {
@@ -285,6 +286,7 @@ void hs_free(hs_handle* hd) {
   cudaFree(hd->d_state);
   cudaFree(hd->lz);
   cudaFree(hd->d_smr_first);
+  sb_release(hd);
   if (hd->h_pinned) cudaFreeHost(hd->h_pinned);
   if (hd->h_state) cudaFreeHost(hd->h_state);
   cudaGetLastError();

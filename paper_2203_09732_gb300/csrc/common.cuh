@@ -142,6 +142,9 @@ struct hs_handle {
   int smr_grid = 0, smr_rows_cap = 0, smr_hdr_cap = 0;
   int* d_smr_first = nullptr;
 
+  // superblock H x plans (hv_sb.cu): [0] FP32, [1] FP64; null where not built
+  void* sb_plan[2] = {nullptr, nullptr};
+
   // Lanczos workspace
   double* lz = nullptr; size_t lz_vectors = 0;
 
@@ -168,6 +171,11 @@ hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int 
 // hv_tma.cu: staged form for blocks of up to 252 rows; *used = false if it does not apply
 hs_status launch_matvec_tma(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted,
                             bool* used);
+// hv_sb.cu: superblock form for long chains; *used = false if it does not apply
+hs_status sb_setup(hs_handle* hd);
+void sb_release(hs_handle* hd);
+hs_status launch_matvec_sb(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted,
+                           bool* used);
 hs_status launch_unrank(hs_handle* hd, long long first, long long count, unsigned int* out);
 hs_status launch_rank(hs_handle* hd, const unsigned int* st, long long count, long long* out);
 hs_status launch_diag(hs_handle* hd, double* diag, hs_precond pc, double* minv);

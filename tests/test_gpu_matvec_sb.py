@@ -1,0 +1,106 @@
+"""GPU parity of the superblock form of H x (row a3 for long chains): the
+matrix-free (H - sigma) x of Eq. (1) with the x tiles of two superblocks
+staged in shared memory, against the oracle's explicit sparse H and against
+the block form."""
+import numpy as np
+import pytest
+
+from oracle import basis, hamiltonian
+from paper_2203_09732_gb300 import inputs
+from tests.gpu_util import need_gpu, to_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("L", [22, 24])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shifted", [0, 1])
+def test_superblock_matvec_vs_oracle(L, dtype, shifted, monkeypatch):
+    """Every row against the explicit matrix (L = 22: 512 pairs of 12-bit
+    superblocks; L = 24: 14-bit superblocks in FP32, 13-bit in FP64)."""
+    hs = need_gpu()
+    monkeypatch.setenv("HS_HV_SB", "1")
+    h = inputs.disorder(L, 3.0, 300 + L)
+    H, diag, st = hamiltonian.build(L, h)
+    sigma = 0.41
+    x = inputs.gaussian(len(st), 17 + L)
+    tdt = torch.float64
+    if dtype == "f32":
+        x = x.astype(np.float32).astype(np.float64)
+        tdt = torch.float32
+    ref = H @ x - (sigma * x if shifted else 0)
+    with hs.Chain(L, h, sigma=sigma) as c:
+        y = c.matvec(to_dev(x, tdt), shifted=bool(shifted)).cpu().double().numpy()
+    if dtype == "f64":
+        scale = np.abs(diag * x).max() + np.abs(x).max() * L
+        assert np.abs(y - ref).max() <= 1e-14 * scale
+    else:
+        s = sigma if shifted else 0.0
+        bound = (L + 4) * 2.0 ** -24 * (np.abs(diag - s) * np.abs(x) + abs(H) @ np.abs(x)) * 2
+        assert (np.abs(y - ref) <= bound + 1e-30).all()
+
+
+@pytest.mark.parametrize("L", [24, 26, 28])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_superblock_matches_block_form(L, dtype, monkeypatch):
+    """Full-size launches: superblock form against the block (gather) form on
+    the same x; the two differ only in the order of the row sums."""
+    hs = need_gpu()
+    h = inputs.disorder(L, 3.7, 4)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    with hs.Chain(L, h, sigma=0.1) as c:
+        x = torch.randn(c.n, generator=torch.Generator().manual_seed(2), dtype=torch.float64).to(tdt).cuda()
+        monkeypatch.setenv("HS_HV_SB", "0")
+        y0 = c.matvec(x, shifted=True)
+        monkeypatch.setenv("HS_HV_SB", "1")
+        y1 = c.matvec(x, shifted=True)
+        torch.cuda.synchronize()
+    assert bool(torch.isfinite(y1).all())
+    scale = float(x.abs().max()) * (L + 3.7 * L)
+    tol = (1e-14 if dtype == "f64" else (L + 4) * 2.0 ** -23) * scale
+    assert float((y1 - y0).abs().max()) <= tol
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("offset", [1, 3])
+def test_superblock_unaligned_vectors(dtype, offset, monkeypatch):
+    """x and y that start off a 16-byte boundary: the staged copies split into
+    element copies at the ends and 16-byte copies in between; the result is
+    the same as with aligned vectors, element for element."""
+    hs = need_gpu()
+    monkeypatch.setenv("HS_HV_SB", "1")
+    L = 24
+    h = inputs.disorder(L, 3.0, 8)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    with hs.Chain(L, h, sigma=0.3) as c:
+        x = torch.randn(c.n, generator=torch.Generator().manual_seed(6), dtype=torch.float64).to(tdt).cuda()
+        y = c.matvec(x, shifted=True)
+        xb = torch.zeros(c.n + 8, dtype=tdt, device="cuda")
+        yb = torch.full((c.n + 8,), float("nan"), dtype=tdt, device="cuda")
+        xb[offset:offset + c.n] = x
+        c.matvec(xb[offset:offset + c.n], y=yb[offset:offset + c.n], shifted=True)
+        torch.cuda.synchronize()
+    assert torch.equal(yb[offset:offset + c.n], y)
+    assert bool(torch.isnan(yb[:offset]).all()) and bool(torch.isnan(yb[offset + c.n:]).all())
+
+
+def test_superblock_sampled_rows_l26(monkeypatch):
+    """L = 26 (10,400,600 rows, 512 pairs of 16-bit superblocks): sampled rows
+    computed one by one from Eq. (1)."""
+    hs = need_gpu()
+    monkeypatch.setenv("HS_HV_SB", "1")
+    L = 26
+    h = inputs.disorder(L, 3.7, 1)
+    n = inputs.dim(L)
+    rng = np.random.default_rng(4)
+    x = torch.randn(n, generator=torch.Generator().manual_seed(9), dtype=torch.float64)
+    sigma = -0.15
+    with hs.Chain(L, h, sigma=sigma) as c:
+        y = c.matvec(x.cuda(), shifted=True).cpu().numpy()
+    xs = x.numpy()
+    for i in np.concatenate([rng.integers(0, n, 200), [0, n - 1]]):
+        s = basis.unrank_count(int(i), L)
+        d, off = hamiltonian.row(L, h, s, sigma)
+        ref = d * xs[i] + sum(v * xs[j] for j, v in off)
+        mag = abs(d * xs[i]) + sum(abs(v * xs[j]) for j, v in off)
+        assert abs(y[i] - ref) <= 1e-14 * mag + 1e-300, (i, y[i], ref)
