@@ -64,9 +64,10 @@ def test_superblock_matches_block_form(L, dtype, monkeypatch):
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("offset", [1, 3])
 def test_superblock_unaligned_vectors(dtype, offset, monkeypatch):
-    """x and y that start off a 16-byte boundary: the staged copies split into
-    element copies at the ends and 16-byte copies in between; the result is
-    the same as with aligned vectors, element for element."""
+    """x and y that start off a 16-byte boundary (views at an element offset):
+    the staged copies and the stores follow the vectors, and the result is
+    the same as with aligned vectors, element for element, with nothing
+    written outside y."""
     hs = need_gpu()
     monkeypatch.setenv("HS_HV_SB", "1")
     L = 24
@@ -85,8 +86,8 @@ def test_superblock_unaligned_vectors(dtype, offset, monkeypatch):
 
 
 def test_superblock_sampled_rows_l26(monkeypatch):
-    """L = 26 (10,400,600 rows, 512 pairs of 16-bit superblocks): sampled rows
-    computed one by one from Eq. (1)."""
+    """L = 26 (10,400,600 rows; FP64 plan: 4096 pairs of 13-bit superblocks):
+    sampled rows computed one by one from Eq. (1)."""
     hs = need_gpu()
     monkeypatch.setenv("HS_HV_SB", "1")
     L = 26
