@@ -17,6 +17,16 @@
  *   - Streams: all work is enqueued on the stream given to hs_create (NULL =
  *     legacy default stream). Calls that return host results synchronise that
  *     stream before returning.
+ *   - Memory: a handle's device memory comes from a memory pool the library
+ *     owns, allocated and freed in order on the handle's stream, so creating
+ *     and freeing handles does not synchronise the device while solves run on
+ *     other streams. Freed memory stays in the pool for later handles until
+ *     the process exits; pinned host staging buffers are likewise reused.
+ *   - Concurrency: handles on separate streams run concurrently. With more
+ *     than 8 busy streams, set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) in the
+ *     environment before the process creates its CUDA context; otherwise
+ *     streams share hardware queues and a short kernel can wait behind
+ *     another stream's persistent solve.
  *   - Errors: every call returns an hs_status; no call aborts, throws or traps.
  *     hs_last_error() returns a message for the last failing call on a handle.
  *     Device-side failures (non-finite values, breakdown) are reported through

@@ -9,8 +9,87 @@
 #include "common.cuh"
 
 #include <atomic>
+#include <map>
+#include <mutex>
 
 namespace hs {
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+static int g_pool_state[64];  // 0 unknown, 1 pool, 2 no pool (plain cudaMalloc)
+
+static cudaMemPool_t pool_for(int dev) {
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool_state[dev] == 0) {
+    g_pool_state[dev] = 2;
+    int ok = 0;
+    if (cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, dev) == cudaSuccess && ok) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t pool;
+      if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+        uint64_t keep = ~0ull;  // keep freed memory in the pool
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+        g_pool_state[dev] = 1;
+      }
+    }
+    cudaGetLastError();
+  }
+  return g_pool_state[dev] == 1 ? g_pool[dev] : nullptr;
+}
+
+hs_status dev_alloc(hs_handle* hd, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 256;
+  cudaMemPool_t pool = pool_for(hd->device);
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, hd->stream)
+                             : cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(hd, HS_OOM, "device allocation failed");
+  }
+  return HS_OK;
+}
+
+void dev_free(hs_handle* hd, void* p) {
+  if (!p) return;
+  if (pool_for(hd->device)) cudaFreeAsync(p, hd->stream);
+  else cudaFree(p);
+}
+
+static std::mutex g_pin_mu;
+static std::multimap<size_t, void*> g_pin_free;
+
+void* host_pinned_get(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    auto it = g_pin_free.find(bytes);
+    if (it != g_pin_free.end()) {
+      void* q = it->second;
+      g_pin_free.erase(it);
+      return q;
+    }
+  }
+  void* q = nullptr;
+  if (cudaMallocHost(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return q;
+}
+
+void host_pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.emplace(bytes, p);
+}
 
 static std::atomic<unsigned long long> g_launches{0};
 void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -35,13 +114,12 @@ int row_grid(const hs_handle* hd) {
 hs_status ensure_reduce(hs_handle* hd) {
   if (hd->d_partial) return HS_OK;
   const size_t nd = (size_t)RED_MAX_CTAS * 4 + 1024 * 512 + 8192;
-  if (cudaMalloc(&hd->d_partial, nd * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(hd, HS_OOM, "reduction scratch allocation failed");
-  }
-  HS_CUDA_TRY(hd, cudaMalloc(&hd->d_counter, 16 * sizeof(unsigned int)));
+  hs_status st = dev_alloc(hd, (void**)&hd->d_partial, nd * sizeof(double));
+  if (st != HS_OK) return st;
+  if ((st = dev_alloc(hd, (void**)&hd->d_counter, 16 * sizeof(unsigned int))) != HS_OK) return st;
   HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_counter, 0, 16 * sizeof(unsigned int), hd->stream));
-  HS_CUDA_TRY(hd, cudaMallocHost(&hd->h_pinned, (size_t)RED_MAX_CTAS * 64 * sizeof(double)));
+  hd->h_pinned = static_cast<double*>(host_pinned_get(PINNED_RED_BYTES));
+  if (!hd->h_pinned) return fail(hd, HS_OOM, "pinned host allocation failed");
   return HS_OK;
 }
 
@@ -170,18 +248,20 @@ static hs_status build_tables(hs_handle* hd) {
 template <typename T>
 static hs_status upload(hs_handle* hd, T** dst, const std::vector<T>& src) {
   const size_t bytes = std::max<size_t>(sizeof(T), src.size() * sizeof(T));
-  if (cudaMalloc(dst, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(hd, HS_OOM, "table allocation failed");
-  }
+  hs_status st = dev_alloc(hd, (void**)dst, bytes);
+  if (st != HS_OK) return st;
+  // pageable source: the copy is staged before the call returns
   if (!src.empty())
-    HS_CUDA_TRY(hd, cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    HS_CUDA_TRY(hd, cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T),
+                                    cudaMemcpyHostToDevice, hd->stream));
   return HS_OK;
 }
 
 hs_status set_sigma_dev(hs_handle* hd, double sigma) {
   hd->sigma = sigma;
-  HS_CUDA_TRY(hd, cudaMemcpy(hd->d_sigma, &hd->sigma, sizeof(double), cudaMemcpyHostToDevice));
+  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->d_sigma, &hd->sigma, sizeof(double), cudaMemcpyHostToDevice,
+                                  hd->stream));
+  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
   return HS_OK;
 }
 
@@ -255,7 +335,7 @@ hs_status hs_create(int L, const double* h_host, double sigma, void* cuda_stream
     if ((st = upload(hd, &hd->d_binom, bt)) != HS_OK) return bail(st);
   }
   if (L >= 22 && (st = sb_setup(hd)) != HS_OK) return bail(st);
-  if (cudaMalloc(&hd->d_sigma, sizeof(double)) != cudaSuccess) { cudaGetLastError(); return bail(HS_OOM); }
+  if ((st = dev_alloc(hd, (void**)&hd->d_sigma, sizeof(double))) != HS_OK) return bail(st);
   if ((st = ensure_reduce(hd)) != HS_OK) return bail(st);
   if (std::isnan(sigma)) {
     double emin, emax, mid;
@@ -275,20 +355,20 @@ void hs_free(hs_handle* hd) {
     if (hd->graph32[i]) cudaGraphExecDestroy(hd->graph32[i]);
     if (hd->graph64[i]) cudaGraphExecDestroy(hd->graph64[i]);
   }
-  cudaFree(hd->d_low);
-  cudaFree(hd->d_blocks);
-  cudaFree(hd->d_binom);
-  cudaFree(hd->d_sigma);
-  cudaFree(hd->d_partial);
-  cudaFree(hd->d_counter);
-  cudaFree(hd->ws32);
-  cudaFree(hd->ws64);
-  cudaFree(hd->d_state);
-  cudaFree(hd->lz);
-  cudaFree(hd->d_smr_first);
+  dev_free(hd, hd->d_low);
+  dev_free(hd, hd->d_blocks);
+  dev_free(hd, hd->d_binom);
+  dev_free(hd, hd->d_sigma);
+  dev_free(hd, hd->d_partial);
+  dev_free(hd, hd->d_counter);
+  dev_free(hd, hd->ws32);
+  dev_free(hd, hd->ws64);
+  dev_free(hd, hd->d_state);
+  dev_free(hd, hd->lz);
+  dev_free(hd, hd->d_smr_first);
   sb_release(hd);
-  if (hd->h_pinned) cudaFreeHost(hd->h_pinned);
-  if (hd->h_state) cudaFreeHost(hd->h_state);
+  host_pinned_put(hd->h_pinned, PINNED_RED_BYTES);
+  host_pinned_put(hd->h_state, sizeof(MinresState));
   cudaGetLastError();
   delete hd;
 }
@@ -363,14 +443,14 @@ hs_status hs_minres(hs_handle* hd, const double* b_dev, double* x_dev, double to
       info->sweeps = 1;
       double sums[4];
       double* r = nullptr;
-      if (cudaMalloc(&r, sizeof(double) * hd->n) == cudaSuccess) {
+      if (dev_alloc(hd, (void**)&r, sizeof(double) * hd->n) == HS_OK) {
         if (resid64(hd, b_dev, x_dev, r, pc, sums) == HS_OK) {
           info->resid_minv = sums[2] > 0 ? std::sqrt(sums[0] / sums[2]) : 0.0;
           info->resid_2 = sums[3] > 0 ? std::sqrt(sums[1] / sums[3]) : 0.0;
         }
-        cudaFree(r);
+        dev_free(hd, r);
       } else {
-        cudaGetLastError();
+        hd->err.clear();
       }
     }
     return st;

@@ -156,6 +156,18 @@ namespace hs {
 // launch accounting -----------------------------------------------------------
 void count_launches(unsigned long long k);
 
+// memory (api.cu) --------------------------------------------------------------
+// Device buffers come from a library-owned memory pool, stream-ordered on the
+// handle's stream (cudaMallocFromPoolAsync / cudaFreeAsync): creating and
+// freeing handles never synchronises the device, so solves on other streams
+// keep running. The pool keeps freed memory for reuse. Pinned host staging
+// blocks come from a process-wide cache and are reused, never released.
+hs_status dev_alloc(hs_handle* hd, void** p, size_t bytes);
+void dev_free(hs_handle* hd, void* p);
+void* host_pinned_get(size_t bytes);
+void host_pinned_put(void* p, size_t bytes);
+constexpr size_t PINNED_RED_BYTES = (size_t)RED_MAX_CTAS * 64 * sizeof(double);
+
 // error helpers -------------------------------------------------------------
 hs_status fail(hs_handle* hd, hs_status st, const std::string& msg);
 #define HS_CUDA_TRY(hd, call)                                                   \

@@ -152,14 +152,14 @@ static hs_status make_dev(hs_handle* hd, int KS, DevPlan** out) {
   const size_t o_sup = put(P.sup.data(), P.sup.size() * sizeof(Sup), s_sup);
   const size_t o_pr = put(P.pairs.data(), P.pairs.size() * sizeof(int2), s_pr);
   DevPlan* d = new DevPlan();
-  if (cudaMalloc(&d->mem, total) != cudaSuccess) {
-    cudaGetLastError();
+  if (dev_alloc(hd, &d->mem, total) != HS_OK) {
     delete d;
     return fail(hd, HS_OOM, "superblock table allocation failed");
   }
-  if (cudaMemcpy(d->mem, host.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+  // pageable source: the copy is staged before the call returns
+  if (cudaMemcpyAsync(d->mem, host.data(), total, cudaMemcpyHostToDevice, hd->stream) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(d->mem);
+    dev_free(hd, d->mem);
     delete d;
     return fail(hd, HS_CUDA, "superblock table upload failed");
   }
@@ -220,7 +220,7 @@ void sb_release(hs_handle* hd) {
   for (int i = 0; i < 2; ++i) {
     auto* d = static_cast<sb::DevPlan*>(hd->sb_plan[i]);
     if (d) {
-      cudaFree(d->mem);
+      dev_free(hd, d->mem);
       delete d;
     }
     hd->sb_plan[i] = nullptr;

@@ -90,13 +90,11 @@ hs_status tridiag_eig(int k, const double* alpha, const double* beta, double* th
 
 static hs_status ensure_lz(hs_handle* hd, size_t nvec) {
   if (hd->lz_vectors >= nvec) return HS_OK;
-  if (hd->lz) cudaFree(hd->lz);
+  dev_free(hd, hd->lz);
   hd->lz = nullptr;
   hd->lz_vectors = 0;
-  if (cudaMalloc(&hd->lz, nvec * sizeof(double) * (size_t)hd->n) != cudaSuccess) {
-    cudaGetLastError();
+  if (dev_alloc(hd, (void**)&hd->lz, nvec * sizeof(double) * (size_t)hd->n) != HS_OK)
     return fail(hd, HS_OOM, "Lanczos basis allocation failed");
-  }
   hd->lz_vectors = nvec;
   return HS_OK;
 }
@@ -312,8 +310,7 @@ extern "C" hs_status hs_eigs_host(int L, const double* h_host, double sigma, int
   if (st != HS_OK) { cudaStreamDestroy(s); return st; }
   hs_set_sm_budget(hd, sm_budget);
   double* ev = nullptr;
-  if (cudaMalloc(&ev, sizeof(double) * (size_t)K * hd->n) != cudaSuccess) {
-    cudaGetLastError();
+  if (dev_alloc(hd, (void**)&ev, sizeof(double) * (size_t)K * hd->n) != HS_OK) {
     hs_free(hd);
     cudaStreamDestroy(s);
     return HS_OOM;
@@ -332,7 +329,7 @@ extern "C" hs_status hs_eigs_host(int L, const double* h_host, double sigma, int
       st = HS_CUDA;
     }
   }
-  cudaFree(ev);
+  dev_free(hd, ev);
   hs_free(hd);
   cudaStreamDestroy(s);
   return st;

@@ -1137,23 +1137,23 @@ static hs_status ensure_ws(hs_handle* hd, MinresVecs& v) {
   void** ws = sizeof(T) == 8 ? &hd->ws64 : &hd->ws32;
   size_t* wsb = sizeof(T) == 8 ? &hd->ws64_bytes : &hd->ws32_bytes;
   if (*wsb < need) {
-    if (*ws) cudaFree(*ws);
+    dev_free(hd, *ws);
     *ws = nullptr; *wsb = 0;
     cudaGraphExec_t* gr = sizeof(T) == 8 ? hd->graph64 : hd->graph32;
     for (int i = 0; i < 3; ++i)
       if (gr[i]) { cudaGraphExecDestroy(gr[i]); gr[i] = nullptr; }
-    if (cudaMalloc(ws, need) != cudaSuccess) {
-      cudaGetLastError();
+    if (dev_alloc(hd, ws, need) != HS_OK)
       return fail(hd, HS_OOM, "MINRES workspace allocation failed");
-    }
     *wsb = need;
   }
   char* b = (char*)*ws;
   v.q0 = b; v.q1 = b + vec; v.d0 = b + 2 * vec; v.d1 = b + 3 * vec; v.p = b + 4 * vec;
   v.x = b + 5 * vec;
   if (!hd->d_state) {
-    HS_CUDA_TRY(hd, cudaMalloc(&hd->d_state, sizeof(MinresState)));
-    HS_CUDA_TRY(hd, cudaMallocHost(&hd->h_state, sizeof(MinresState)));
+    hs_status st = dev_alloc(hd, (void**)&hd->d_state, sizeof(MinresState));
+    if (st != HS_OK) return st;
+    hd->h_state = static_cast<MinresState*>(host_pinned_get(sizeof(MinresState)));
+    if (!hd->h_state) return fail(hd, HS_OOM, "pinned host allocation failed");
   }
   return ensure_reduce(hd);
 }
@@ -1241,11 +1241,15 @@ static hs_status smr_plan(hs_handle* hd, int G, int** d_first, int* rows_cap, in
     hc = std::max(hc, hi - lo);
   }
   rc = (rc + 3) & ~3;
-  if (hd->d_smr_first) cudaFree(hd->d_smr_first);
+  dev_free(hd, hd->d_smr_first);
   hd->d_smr_first = nullptr;
-  HS_CUDA_TRY(hd, cudaMalloc(&hd->d_smr_first, sizeof(int) * (G + 1)));
-  HS_CUDA_TRY(hd, cudaMemcpy(hd->d_smr_first, first.data(), sizeof(int) * (G + 1),
-                             cudaMemcpyHostToDevice));
+  {
+    hs_status st = dev_alloc(hd, (void**)&hd->d_smr_first, sizeof(int) * (G + 1));
+    if (st != HS_OK) return st;
+  }
+  // pageable source: the copy is staged before the call returns
+  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->d_smr_first, first.data(), sizeof(int) * (G + 1),
+                                  cudaMemcpyHostToDevice, hd->stream));
   hd->smr_grid = G; hd->smr_rows_cap = rc; hd->smr_hdr_cap = hc;
   *d_first = hd->d_smr_first; *rows_cap = rc; *hdr_cap = hc;
   return HS_OK;
@@ -1352,7 +1356,9 @@ static hs_status solve_cluster_v(hs_handle* hd, const T* b, const MinresVecs& v,
     return HS_CUDA;
   }
   std::vector<int> fh(CS + 1);
-  HS_CUDA_TRY(hd, cudaMemcpy(fh.data(), first, sizeof(int) * (CS + 1), cudaMemcpyDeviceToHost));
+  HS_CUDA_TRY(hd, cudaMemcpyAsync(fh.data(), first, sizeof(int) * (CS + 1), cudaMemcpyDeviceToHost,
+                                  hd->stream));
+  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
   ClusterMap cm;
   for (int c = 0; c < 17; ++c) cm.rstart[c] = (uint32_t)hd->n;
   for (int c = 0; c < CS; ++c) cm.rstart[c] = fh[c] < (int)hd->blocks.size() ? hd->blocks[fh[c]].R : (uint32_t)hd->n;
