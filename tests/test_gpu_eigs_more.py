@@ -93,3 +93,45 @@ def test_host_buffers_end_to_end_with_budget():
     ov = np.abs(np.einsum("in,ni->i", vec, V[:, idx]))
     assert (ov > 1 - 1e-8).all()
     assert np.abs(np.abs(z) ** 2 - np.abs(twist.overlap(V[:, idx], st, L)) ** 2).max() < 1e-8
+
+
+def test_concurrent_handles_reuse_pool_memory():
+    """Handles on separate streams created, solved and freed at the same time
+    by several host threads. Device memory comes from the library's
+    stream-ordered pool, so a freed handle's memory is reused by a handle on
+    another stream. Every eigensolve must match dense eigh, whatever the
+    interleaving."""
+    import threading
+    hs = need_gpu()
+    L, K = 10, 4
+    cases = []
+    for i in range(6):
+        hv = inputs.disorder(L, 1.0 + 0.5 * i, 40 + i)
+        H, diag, st = hamiltonian.build(L, hv)
+        w = np.linalg.eigvalsh(H.toarray())
+        sigma = 0.5 * (w[0] + w[-1])
+        cases.append((hv, sigma, w[np.lexsort((w, np.abs(w - sigma)))[:K]]))
+    errors = []
+
+    def worker(tid):
+        s = torch.cuda.Stream()
+        try:
+            for rep in range(3):
+                for j, (hv, sigma, ref) in enumerate(cases):
+                    if (j + tid) % 2:
+                        continue
+                    with torch.cuda.stream(s):
+                        with hs.Chain(L, hv, sigma=sigma, stream=s) as c:
+                            c.set_sm_budget(8)
+                            ev, _, _, info = c.eigs(K, seed=rep + 1, vectors=False)
+                    if np.abs(ev - ref).max() > 1e-10 or info["converged"] != K:
+                        errors.append((tid, rep, j, float(np.abs(ev - ref).max())))
+        except Exception as e:  # pragma: no cover - reported below
+            errors.append((tid, repr(e)))
+
+    th = [threading.Thread(target=worker, args=(t,)) for t in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
