@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_persist(Geo g, const T* _
 // Rows of one block whose own segment (self and low-interior neighbours) is
 // read from shared memory xl; the other gathers come from global xg.
 template <typename T, int JM>
-__device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* xl,
+__device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* xl, const T* dg,
                                              const LowEntry* low, const Hdr& h, T (&xi)[JM],
                                              T (&hx)[JM]) {
   const int lane = threadIdx.x & 31;
@@ -417,7 +417,6 @@ __device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* 
     if (j < h.J && r < h.C) {
       const LowEntry& e = low[h.off + r];
       const uint32_t pk = e.packed;
-      const uint32_t xc = cut_mask(pk, h);
       T acc = hx[j] + side[j];
       const int cnt = le_cnt(pk);
       const uint32_t w0 = e.nbw[0], w1 = e.nbw[1], w2 = e.nbw[2];
@@ -426,7 +425,7 @@ __device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* 
         const uint32_t wd = m < 4 ? w0 : (m < 8 ? w1 : w2);
         if (m < cnt) acc += xl[(wd >> (8 * (m & 3))) & 0xFFu];
       }
-      hx[j] = diag_t<T>(e, h, xc) * xi[j] + T(0.5) * acc;
+      hx[j] = dg[r] * xi[j] + T(0.5) * acc;
     }
   }
 }
@@ -534,7 +533,7 @@ template <typename T>
 __host__ __device__ inline size_t smr_bytes(int nlow, int hdr_cap, int rows_cap, int nt) {
   size_t b = sizeof(LowEntry) * (size_t)nlow + 128 * (size_t)hdr_cap;
   b = (b + 15) & ~size_t(15);
-  b += 8 * sizeof(T) * (size_t)rows_cap;
+  b += 9 * sizeof(T) * (size_t)rows_cap;
   b = (b + 15) & ~size_t(15);
   return b + sizeof(double) * (sizeof(T) == 8 ? 2 * (size_t)nt : 64);
 }
@@ -606,7 +605,8 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem(
   T* X = QL0 + 5 * rows_cap;
   T* MV = QL0 + 6 * rows_cap;        // M_ii
   T* MI = QL0 + 7 * rows_cap;        // 1 / M_ii
-  off += 8 * sizeof(T) * (size_t)rows_cap;
+  T* DG = QL0 + 8 * rows_cap;        // a_ii - sigma (rebuilding it costs ~4 FP64 operations a row)
+  off += 9 * sizeof(T) * (size_t)rows_cap;
   off = (off + 15) & ~size_t(15);
   double* stmp = reinterpret_cast<double*>(smem + off);
   const uint32_t Rbase = __ldg(&g.blocks[b0].R);
@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem(
         zm += (m == T(0)) ? T(1) : T(0);
         const T mi = m == T(0) ? T(0) : T(1) / m;
         const T q = b * mi;
-        MV[l] = m; MI[l] = mi;
+        MV[l] = m; MI[l] = mi; DG[l] = am;
         QL1[l] = q; qg1[i] = q;
         QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
         acc += q * b;
@@ -696,7 +696,7 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem(
         }
       if (doMV) {
         T xi[JM], hx[JM];
-        block_hv_loc<T, JM>(qgc, QLc + l0, low, h, xi, hx);
+        block_hv_loc<T, JM>(qgc, QLc + l0, DG + l0, low, h, xi, hx);
 #pragma unroll
         for (int j = 0; j < JM; ++j) {
           const int r = lane + 32 * j;
