@@ -406,10 +406,13 @@ __device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* 
       for (int j = 0; j < JM; ++j)
         v[mm][j] = (on && j < h.J && lane + 32 * j < h.C) ? ldx<T, true>(xh + 32 * j) : T(0);
     }
+    // only the bonds that exist: the count is the same for the whole warp, so
+    // this skips FP64 adds of zero (the FP64 pipe bounds this pass)
 #pragma unroll
     for (int mm = 0; mm < HG; ++mm)
+      if (m0 + mm < h.nh)
 #pragma unroll
-      for (int j = 0; j < JM; ++j) hx[j] += v[mm][j];
+        for (int j = 0; j < JM; ++j) hx[j] += v[mm][j];
   }
 #pragma unroll
   for (int j = 0; j < JM; ++j) {
