@@ -122,9 +122,14 @@ hs_status hs_rank(hs_handle* hd, const unsigned int* states_dev, long long count
 hs_status hs_diag(hs_handle* hd, double* diag_dev, hs_precond pc, double* minv_dev);
 
 /* Matrix-free y = H x (shifted = 0) or y = (H - sigma) x (shifted = 1), in
- * FP32 (x, y float, FP32 accumulation) or FP64. x and y must not overlap.
+ * FP32 (x, y float, FP32 accumulation) or FP64. x and y must not overlap and
+ * must be aligned to their element size (any offset from that is fine).
  * Eq. (1); element (i, k) for i != k is 1/2 exactly when states i and k differ
- * by the flip of one antiparallel bond (Appendix C). */
+ * by the flip of one antiparallel bond (Appendix C). From L = 24 on, FP32 uses
+ * the superblock form (x of two superblocks staged in shared memory); the
+ * environment variable HS_HV_SB=0 selects the block form, HS_HV_SB=1 the
+ * superblock form for both precisions from L = 22 on. Both forms give the
+ * same values up to the order of the row sums. */
 hs_status hs_matvec(hs_handle* hd, const void* x_dev, void* y_dev, hs_dtype dtype,
                     int shifted);
 

@@ -425,6 +425,9 @@ hs_status hs_matvec(hs_handle* hd, const void* x_dev, void* y_dev, hs_dtype dtyp
   if (!hd) return HS_BAD_ARG;
   if (!x_dev || !y_dev || x_dev == y_dev) return fail(hd, HS_BAD_ARG, "hs_matvec: bad pointers");
   if (dtype != HS_F32 && dtype != HS_F64) return fail(hd, HS_BAD_ARG, "hs_matvec: bad dtype");
+  const uintptr_t es = dtype == HS_F32 ? sizeof(float) : sizeof(double);
+  if ((uintptr_t)x_dev % es || (uintptr_t)y_dev % es)
+    return fail(hd, HS_BAD_ARG, "hs_matvec: vectors not aligned to their element size");
   return launch_matvec(hd, x_dev, y_dev, dtype, shifted ? 1 : 0);
 }
 
