@@ -105,3 +105,25 @@ def test_superblock_sampled_rows_l26(monkeypatch):
         ref = d * xs[i] + sum(v * xs[j] for j, v in off)
         mag = abs(d * xs[i]) + sum(abs(v * xs[j]) for j, v in off)
         assert abs(y[i] - ref) <= 1e-14 * mag + 1e-300, (i, y[i], ref)
+
+
+@pytest.mark.parametrize("dtype,es", [("f32", 4), ("f64", 8)])
+def test_matvec_rejects_vectors_off_element_alignment(dtype, es):
+    """A device pointer that is not a multiple of the element size is refused
+    on the host with HS_BAD_ARG, before any launch; the handle stays usable."""
+    import ctypes
+    hs = need_gpu()
+    L = 24
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    with hs.Chain(L, inputs.disorder(L, 1.0, 2), sigma=0.0) as c:
+        x = torch.randn(c.n + 2, dtype=tdt, device="cuda")
+        y = torch.zeros(c.n + 2, dtype=tdt, device="cuda")
+        dt = hs.F64 if dtype == "f64" else hs.F32
+        for dx, dy in ((es // 2, 0), (0, es // 2)):
+            st = c._lib.hs_matvec(c._hd, ctypes.c_void_p(x.data_ptr() + dx),
+                                  ctypes.c_void_p(y.data_ptr() + dy), dt, 1)
+            assert st == hs.HS_BAD_ARG
+        assert float(y.abs().max()) == 0.0
+        y1 = c.matvec(x[:c.n], shifted=True)
+        torch.cuda.synchronize()
+        assert bool(torch.isfinite(y1).all())
