@@ -8,9 +8,10 @@ Workload: the L = 16 part of the batched disorder sweep (dimension 12870;
 per realisation h ~ U[0.5, 6], then h_j ~ U[-h, h]; sigma at the spectrum
 midpoint E_min/E_max; the 8 eigenpairs nearest sigma). One step = one batch of
 B = 24 seeded realisations solved concurrently on one GPU (24 streams, each
-persistent MINRES on 6 of the 152 SMs; the solve is latency-bound, so 24
-narrow solves gave 1.7x the eigenpairs/s of 8 wide ones), every realisation
-end to end:
+persistent MINRES on 6 of the 152 SMs at first; the solve is latency-bound, so
+24 narrow solves gave 1.7x the eigenpairs/s of 8 wide ones; as realisations
+finish, the others take over their SMs from the next Lanczos step), every
+realisation end to end:
 sigma by extremal Lanczos, shift-invert Lanczos with full reorthogonalisation,
 MINRES with the row-norm preconditioner in every step, Ritz pairs certified by
 FP64 residuals, twist overlaps. The value is eigenpairs per second over the
@@ -51,6 +52,8 @@ sys.path.insert(0, ROOT)
 METRIC = "eigenpairs/s near sigma at L=28 (FP32+refine vs FP64); H*v GB/s vs HBM peak"
 UNIT = "eigenpairs/s"
 BATCH = 24
+SHARE_CAP = 38   # SMs per solve when few realisations are left (beyond this the
+                 # L = 16 iteration is latency-bound and gains little)
 FALLBACK_HBM_GBS = 6800.0
 # Lanczos steps per wanted eigenpair in the paper: m = 130 for 50 eigenpairs (Sec. IV A).
 PAPER_M_PER_PAIR = 130.0 / 50.0
@@ -83,6 +86,8 @@ def parse():
     ap.add_argument("--minres-tol", type=float, default=1e-10, dest="minres_tol")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--static-budget", action="store_true", dest="static_budget",
+                    help="keep every realisation on nsm // batch SMs for the whole step")
     ap.add_argument("--only", choices=["hv", "minres"], default=None,
                     help="profiling cases: only the H x timing (--hv-L), or one FP64 MINRES "
                          "solve of --minres-iters iterations at --L")
@@ -343,16 +348,48 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def solve_one(idx, mixed, out):
+    class Shares:
+        """SM shares of the realisations running in one step. When one
+        finishes, the others get its SMs from their next Lanczos step on
+        (the library reads the share at every MINRES solve); the shares of
+        running solves never sum to more than the SM count."""
+
+        def __init__(self, n):
+            self.lock = threading.Lock()
+            self.live = {}
+            self.active = n
+
+        def share(self):
+            if args.static_budget:
+                return budget
+            return max(budget, min(SHARE_CAP, nsm // max(1, self.active)))
+
+        def start(self, key, c):
+            with self.lock:
+                self.live[key] = c
+                c.set_sm_budget(self.share())
+
+        def done(self, key):
+            with self.lock:
+                self.live.pop(key, None)
+                self.active -= 1
+                b = self.share()
+                for other in self.live.values():
+                    other.set_sm_budget(b)
+
+    def solve_one(idx, mixed, out, shares):
         h, seed, hv = realisation(idx, L)
         s = torch.cuda.Stream()
         t0 = time.perf_counter()
         with torch.cuda.stream(s):
             with hs.Chain(L, hv, stream=s) as c:
-                c.set_sm_budget(budget)
-                ev, vecs, res, info = c.eigs(K, mixed=mixed, minres_tol=args.minres_tol, seed=seed,
-                                             allow_not_converged=True)
-                z = c.twist(vecs)
+                shares.start(idx, c)
+                try:
+                    ev, vecs, res, info = c.eigs(K, mixed=mixed, minres_tol=args.minres_tol,
+                                                 seed=seed, allow_not_converged=True)
+                    z = c.twist(vecs)
+                finally:
+                    shares.done(idx)
             s.synchronize()
         out.append({"h": round(h, 4), "seed": seed, "seconds": time.perf_counter() - t0,
                     "lanczos_steps": info["steps"], "minres_iters": info["minres_iters"],
@@ -362,8 +399,9 @@ def run_ours(args):
     def batch(step_idx, mixed, out):
         """One step: B realisations solved concurrently (one host thread and
         one stream each; ctypes releases the GIL inside the library)."""
-        th = [threading.Thread(target=solve_one, args=(idx, mixed, out))
-              for idx in rank_realisations(rank, world, step_idx, B)]
+        idxs = rank_realisations(rank, world, step_idx, B)
+        shares = Shares(len(idxs))
+        th = [threading.Thread(target=solve_one, args=(idx, mixed, out, shares)) for idx in idxs]
         for t in th:
             t.start()
         for t in th:
@@ -479,6 +517,7 @@ def run_ours(args):
                                f"Sz=0 (dim {n}), {K} eigenpairs nearest sigma=(Emin+Emax)/2 per "
                                f"realisation, {B} realisations per step solved concurrently",
                    "L": L, "K": K, "batch": B, "sm_per_realisation": budget,
+                   "sm_shares": "static" if args.static_budget else f"rebalanced as realisations finish (up to {SHARE_CAP} SMs each)",
                    "minres_tol": args.minres_tol, "precond": "row-norm",
                    "l2": "per-realisation working set < 1 MB (L2-resident); H x roofline inputs 321 MB > L2",
                    "parallelism": f"replicas x{world}"},

@@ -216,7 +216,12 @@ hs_status hs_tridiag_eig(int k, const double* alpha, const double* beta, double*
 /* Limit the persistent MINRES solves of this handle to nsm SMs (0 = all).
  * Independent handles on separate streams, each with a share of the SMs, then
  * solve their systems concurrently (several disorder realisations at once).
- * The paper runs one realisation per GPU; this is a throughput setting only. */
+ * The share is read at the start of every MINRES solve, so another host thread
+ * may change it while hs_lanczos_eigs runs on this handle: the new share takes
+ * effect from the next Lanczos step (for example, to hand the SMs of finished
+ * realisations to the ones still running). Keep the shares of concurrent
+ * handles summing to at most the SM count. The paper runs one realisation per
+ * GPU; this is a throughput setting only. */
 hs_status hs_set_sm_budget(hs_handle* hd, int nsm);
 
 /* Number of CUDA kernels this library has launched in the process so far

@@ -376,7 +376,7 @@ void hs_free(hs_handle* hd) {
 hs_status hs_set_sm_budget(hs_handle* hd, int nsm) {
   if (!hd) return HS_BAD_ARG;
   if (nsm < 0) return fail(hd, HS_BAD_ARG, "hs_set_sm_budget: negative SM count");
-  hd->sm_budget = nsm;
+  hd->sm_budget.store(nsm, std::memory_order_relaxed);
   return HS_OK;
 }
 

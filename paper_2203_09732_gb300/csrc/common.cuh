@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -138,7 +139,9 @@ struct hs_handle {
   cudaGraphExec_t graph64[3] = {nullptr, nullptr, nullptr};
 
   // shared-memory-resident MINRES plan
-  int sm_budget = 0;                 // SMs a persistent solve may use (0 = all)
+  // SMs a persistent solve may use (0 = all); read once at the start of each
+  // solve, and may be set from another host thread while a solve runs
+  std::atomic<int> sm_budget{0};
   int smr_grid = 0, smr_rows_cap = 0, smr_hdr_cap = 0;
   int* d_smr_first = nullptr;
 

@@ -1262,7 +1262,8 @@ static hs_status smr_plan(hs_handle* hd, int G, int** d_first, int* rows_cap, in
 template <typename T, int PC, int JM, int NT>
 static hs_status solve_smem_v(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
                               long long kmax) {
-  const int G = std::max(1, std::min(hd->num_sms, hd->sm_budget > 0 ? hd->sm_budget : hd->num_sms));
+  const int bud = hd->sm_budget.load(std::memory_order_relaxed);
+  const int G = std::max(1, std::min(hd->num_sms, bud > 0 ? bud : hd->num_sms));
   int* first = nullptr;
   int rows_cap = 0, hdr_cap = 0;
   hs_status st = smr_plan(hd, G, &first, &rows_cap, &hdr_cap);
@@ -1428,7 +1429,8 @@ static int persist_grid(hs_handle* hd, size_t sm) {
     cudaGetLastError();
     return 0;
   }
-  const int sms = hd->sm_budget > 0 ? std::min(hd->sm_budget, hd->num_sms) : hd->num_sms;
+  const int bud = hd->sm_budget.load(std::memory_order_relaxed);
+  const int sms = bud > 0 ? std::min(bud, hd->num_sms) : hd->num_sms;
   const int cap = std::min(per_sm, 4) * sms;
   return std::min(cap, row_grid(hd));
 }
