@@ -59,6 +59,43 @@ FALLBACK_HBM_GBS = 6800.0
 PAPER_M_PER_PAIR = 130.0 / 50.0
 
 
+class Shares:
+    """SM shares of the realisations running in one step. Every realisation
+    starts on `base` SMs; when one finishes, the others get
+    nsm // (number still running) SMs each (at most `cap`, never less than
+    `base`) from their next Lanczos step on: the library reads a handle's share
+    at every MINRES solve. The shares of running solves never sum to more than
+    nsm. `static` keeps every share at `base`."""
+
+    def __init__(self, n, base, nsm, cap=SHARE_CAP, static=False):
+        self.lock = threading.Lock()
+        self.live = {}
+        self.active = n
+        self.base, self.nsm, self.cap, self.static = base, nsm, cap, static
+        self.current = None
+
+    def share(self):
+        if self.static:
+            return self.base
+        return max(self.base, min(self.cap, self.nsm // max(1, self.active)))
+
+    def start(self, key, chain):
+        with self.lock:
+            self.live[key] = chain
+            self.current = self.share()
+            chain.set_sm_budget(self.current)
+
+    def done(self, key):
+        with self.lock:
+            self.live.pop(key, None)
+            self.active -= 1
+            b = self.share()
+            if b != self.current:
+                self.current = b
+                for other in self.live.values():
+                    other.set_sm_budget(b)
+
+
 def realisation(idx, L):
     """Realisation idx of the batched sweep: h ~ U[0.5, 6], h_j ~ U[-h, h]."""
     from paper_2203_09732_gb300 import inputs
@@ -348,35 +385,6 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    class Shares:
-        """SM shares of the realisations running in one step. When one
-        finishes, the others get its SMs from their next Lanczos step on
-        (the library reads the share at every MINRES solve); the shares of
-        running solves never sum to more than the SM count."""
-
-        def __init__(self, n):
-            self.lock = threading.Lock()
-            self.live = {}
-            self.active = n
-
-        def share(self):
-            if args.static_budget:
-                return budget
-            return max(budget, min(SHARE_CAP, nsm // max(1, self.active)))
-
-        def start(self, key, c):
-            with self.lock:
-                self.live[key] = c
-                c.set_sm_budget(self.share())
-
-        def done(self, key):
-            with self.lock:
-                self.live.pop(key, None)
-                self.active -= 1
-                b = self.share()
-                for other in self.live.values():
-                    other.set_sm_budget(b)
-
     def solve_one(idx, mixed, out, shares):
         h, seed, hv = realisation(idx, L)
         s = torch.cuda.Stream()
@@ -400,7 +408,7 @@ def run_ours(args):
         """One step: B realisations solved concurrently (one host thread and
         one stream each; ctypes releases the GIL inside the library)."""
         idxs = rank_realisations(rank, world, step_idx, B)
-        shares = Shares(len(idxs))
+        shares = Shares(len(idxs), budget, nsm, static=args.static_budget)
         th = [threading.Thread(target=solve_one, args=(idx, mixed, out, shares)) for idx in idxs]
         for t in th:
             t.start()
