@@ -76,6 +76,9 @@ typedef struct {
   double max_resid;    /* max_i ||H psi_i - E_i psi_i||_2 (FP64, certified)       */
   double seconds_solve;   /* host wall time inside the MINRES solves             */
   double seconds_total;   /* host wall time of the whole call                    */
+  int unconverged_solves; /* MINRES solves that stopped at their iteration cap   */
+                          /* (50 n) before minres_tol; the step still used them  */
+  int pad;
 } hs_lanczos_info;
 
 /* Create a handle for chain length L (even, 4 <= L <= 32) and fields
@@ -198,10 +201,12 @@ hs_status hs_twist(hs_handle* hd, const double* psi_dev, int K, double* z_host);
  *   enqueued (asynchronous, nothing is synchronised).
  * Scratch: a fixed 512 KiB static device array inside this library (held by
  * every GPU that loads it until the process exits); no cudaMalloc, cudaFree
- * or allocating library routine is called. The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. Every call shares
- * the array and its arrival counter: calls whose work overlaps on the GPU (for
+ * or allocating library routine is called. Each call made outside a stream
+ * capture looks up the array's device address (cudaGetSymbolAddress) with the
+ * current device; a call inside a capture reuses the address found by the last
+ * uncaptured call on that device, so make one call on each device before any
+ * stream capture (and again after a cudaDeviceReset). Every call shares the
+ * array and its arrival counter: calls whose work overlaps on the GPU (for
  * example on two streams at once) race and must be serialised by the caller. */
 hs_status hs_twist_noalloc(int L, const double* psi_dev, int K, double* z_dev,
                            void* cuda_stream);

@@ -183,9 +183,6 @@ hs_status fail(hs_handle* hd, hs_status st, const std::string& msg);
 
 // launchers implemented in hv.cu -------------------------------------------
 hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted);
-// hv_tma.cu: staged form for blocks of up to 252 rows; *used = false if it does not apply
-hs_status launch_matvec_tma(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted,
-                            bool* used);
 // hv_sb.cu: superblock form for long chains; *used = false if it does not apply
 hs_status sb_setup(hs_handle* hd);
 void sb_release(hs_handle* hd);

@@ -147,13 +147,6 @@ static hs_status prep_smem(hs_handle* hd, K kern, size_t bytes) {
 }
 
 hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted) {
-  if (const char* e = getenv("HS_HV_TMA")) {
-    if (e[0] == '1') {
-      bool used = false;
-      hs_status st = launch_matvec_tma(hd, x, y, dt, shifted, &used);
-      if (st != HS_OK || used) return st;
-    }
-  }
   {
     // superblock form: the FP32 default from L = 24 on (1.2-1.3x faster than
     // the block form there); in FP64 the FP64 pipe bounds both forms and the

@@ -13,10 +13,10 @@
 
 namespace hs {
 
-// Symmetric tridiagonal eigenproblem by implicit QL iterations with a
-// Wilkinson-type shift (the published QL algorithm of Bowdler, Martin,
-// Reinsch & Wilkinson, Numer. Math. 11 (1968)), accumulating the rotations
-// into Y. d: diagonal (overwritten by eigenvalues), e: off-diagonal.
+// Symmetric tridiagonal eigenproblem by the implicit QL algorithm with a
+// Wilkinson-type shift (Martin & Wilkinson, "The implicit QL algorithm",
+// Numer. Math. 12 (1968); the EISPACK routine imtql2), accumulating the plane
+// rotations into Y. d: diagonal (overwritten by eigenvalues), e: off-diagonal.
 hs_status tridiag_eig(int k, const double* alpha, const double* beta, double* theta, double* Y) {
   std::vector<double> d(alpha, alpha + k), e(k, 0.0);
   for (int i = 0; i + 1 < k; ++i) e[i] = beta[i];
@@ -204,6 +204,10 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
     solve_s += std::chrono::duration<double>(clk::now() - ts).count();
     if (info) { info->minres_iters += mi.iters; info->sweeps += mixed ? mi.sweeps : 1; }
     if (st != HS_OK && st != HS_NOT_CONVERGED) return st;
+    // a solve that hit its iteration cap feeds an inexact (H - sigma)^-1 v_k
+    // into the recurrence; the final FP64 residuals still certify the pairs,
+    // and the count is reported
+    if (st == HS_NOT_CONVERGED && info) ++info->unconverged_solves;
     // w = x - beta_k v_{k-1}; alpha_k = v_k . w; w -= alpha_k v_k
     HS_CUDA_TRY(hd, cudaMemcpyAsync(w, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, hd->stream));
     if (k > 0 && (st = vaxpby(hd, -beta_k, V + (size_t)(k - 1) * n, 1.0, w, n)) != HS_OK) return st;

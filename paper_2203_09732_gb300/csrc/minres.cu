@@ -761,299 +761,6 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem(
   }
 }
 
-// ---------------------------------------------------------------------------
-// Cluster form: one solve on one thread-block cluster of CS CTAs (CS SMs).
-// Every CTA owns a contiguous range of blocks and keeps its rows of all
-// vectors (both q iterates, p, two d's, x, M, 1/M) in shared memory. The
-// off-diagonal gathers of q read the owning CTA's shared memory through the
-// cluster's distributed shared memory; a gather target block never straddles
-// two CTAs, so the remote base is resolved once per block and bond. Both
-// reductions exchange partial sums through DSMEM slots and the hardware
-// cluster barrier: no global memory, no software spin-wait. Same arithmetic
-// and order as k_minres_smem.
-struct ClusterMap {
-  uint32_t rstart[17];   // first global row of each CTA, rstart[CS] = n
-};
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ uint32_t dsmem_map(uint32_t addr, uint32_t rank) {
-  uint32_t r;
-  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ T ld_dsmem(uint32_t addr) {
-  if constexpr (sizeof(T) == 8) {
-    double v;
-    asm("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
-    return v;
-  } else {
-    float v;
-    asm("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-    return v;
-  }
-}
-__device__ __forceinline__ void st_dsmem_f64(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-// Shared-memory address (in the owning CTA) of global row t of the vector whose
-// local copy starts at shared address base.
-template <typename T>
-__device__ __forceinline__ uint32_t remote_row(const ClusterMap& cm, int CS, uint32_t base,
-                                               uint32_t t) {
-  int c = 0;
-  while (c + 1 < CS && cm.rstart[c + 1] <= t) ++c;
-  return dsmem_map(base + (t - cm.rstart[c]) * (uint32_t)sizeof(T), (uint32_t)c);
-}
-
-template <typename T, int JM>
-__device__ __forceinline__ void block_hv_cl(const Geo& g, const ClusterMap& cm, int CS,
-                                            uint32_t qbase, const T* xl, const LowEntry* low,
-                                            const Hdr& h, T (&xi)[JM], T (&hx)[JM]) {
-  const int lane = threadIdx.x & 31;
-  constexpr uint32_t W = sizeof(T);
-  // cut bond partner block: the next block (H bit 0 clear) or the previous one;
-  // when the block has no cut-bond flips the partner may not exist, so the
-  // start is clamped to a real row (the address is then never loaded)
-  uint32_t cut_start = (h.code & 1) ? h.R - (uint32_t)g.cls_C[h.w + 1] : h.R + (uint32_t)h.C;
-  if ((int32_t)cut_start < 0 || cut_start >= g.n) cut_start = h.R;
-  const uint32_t cut_base = remote_row<T>(cm, CS, qbase, cut_start) +
-                            (uint32_t)((int32_t)(h.R - cut_start) + h.bdelta) * W;
-  const uint32_t wrap_base = remote_row<T>(cm, CS, qbase, h.Rwrap);
-  T side[JM];
-#pragma unroll
-  for (int j = 0; j < JM; ++j) {
-    xi[j] = T(0);
-    side[j] = T(0);
-    hx[j] = T(0);
-    const int r = lane + 32 * j;
-    if (j < h.J && r < h.C) {
-      const LowEntry& e = low[h.off + r];
-      const uint32_t xc = cut_mask(e.packed, h);
-      xi[j] = xl[r];
-      const T c1 = (xc & 1u) ? ld_dsmem<T>(cut_base + (uint32_t)r * W) : T(0);
-      const T c2 = (xc & 2u) ? ld_dsmem<T>(wrap_base + (uint32_t)e.wrap_r * W) : T(0);
-      side[j] = c1 + c2;
-    }
-  }
-  for (int m = 0; m < h.nh; ++m) {
-    const uint32_t rb = remote_row<T>(cm, CS, qbase, h.R + (uint32_t)hdr_hd(h, m));
-#pragma unroll
-    for (int j = 0; j < JM; ++j)
-      if (j < h.J && lane + 32 * j < h.C) hx[j] += ld_dsmem<T>(rb + (uint32_t)(lane + 32 * j) * W);
-  }
-#pragma unroll
-  for (int j = 0; j < JM; ++j) {
-    const int r = lane + 32 * j;
-    if (j < h.J && r < h.C) {
-      const LowEntry& e = low[h.off + r];
-      const uint32_t pk = e.packed;
-      const uint32_t xc = cut_mask(pk, h);
-      T acc = hx[j] + side[j];
-      const int cnt = le_cnt(pk);
-      const uint32_t w0 = e.nbw[0], w1 = e.nbw[1], w2 = e.nbw[2];
-#pragma unroll
-      for (int mm = 0; mm < NB_MAX; ++mm) {
-        const uint32_t wd = mm < 4 ? w0 : (mm < 8 ? w1 : w2);
-        if (mm < cnt) acc += xl[(wd >> (8 * (mm & 3))) & 0xFFu];
-      }
-      hx[j] = diag_t<T>(e, h, xc) * xi[j] + T(0.5) * acc;
-    }
-  }
-}
-
-template <typename T>
-__host__ __device__ inline size_t cl_bytes(int nlow, int hdr_cap, int rows_cap, int nt) {
-  size_t b = sizeof(LowEntry) * (size_t)nlow + 128 * (size_t)hdr_cap;
-  b = (b + 15) & ~size_t(15);
-  b += 8 * sizeof(T) * (size_t)rows_cap;
-  b = (b + 15) & ~size_t(15);
-  b += sizeof(double) * (sizeof(T) == 8 ? 2 * (size_t)nt : 64);
-  return b + sizeof(double) * 2 * 2 * 16;   // reduction slots: 2 buffers x 16 CTAs x 2
-}
-
-template <typename T, int PC, int JM, int NT>
-__global__ void __launch_bounds__(NT, 1) k_minres_cluster(
-    Geo g, const T* __restrict__ bv, T* xout, MinresState* st, double tol, long long kmax,
-    const double* d_sigma, const int* __restrict__ cta_first, int rows_cap, int hdr_cap,
-    ClusterMap cm, int CS) {
-  extern __shared__ __align__(16) char smem[];
-  __shared__ MinresState S;
-  __shared__ double s_ib, s_ibp;
-  const uint32_t me = cluster_rank();
-  LowEntry* low = reinterpret_cast<LowEntry*>(smem);
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(g.low);
-    uint4* dst = reinterpret_cast<uint4*>(low);
-    for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
-  }
-  const int b0 = cta_first[me], nbk = cta_first[me + 1] - b0;
-  uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * g.nlow);
-  {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
-    for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
-  }
-  // identical layout in every CTA (sized by hdr_cap), so a row's shared
-  // address differs between CTAs only by the CTA's row offset
-  size_t off = sizeof(LowEntry) * g.nlow + 128 * (size_t)hdr_cap;
-  off = (off + 15) & ~size_t(15);
-  T* QL0 = reinterpret_cast<T*>(smem + off);
-  T* QL1 = QL0 + rows_cap;
-  T* P = QL0 + 2 * rows_cap;
-  T* D0 = QL0 + 3 * rows_cap;
-  T* D1 = QL0 + 4 * rows_cap;
-  T* X = QL0 + 5 * rows_cap;
-  T* MV = QL0 + 6 * rows_cap;
-  T* MI = QL0 + 7 * rows_cap;
-  off += 8 * sizeof(T) * (size_t)rows_cap;
-  off = (off + 15) & ~size_t(15);
-  double* stmp = reinterpret_cast<double*>(smem + off);
-  off += sizeof(double) * (sizeof(T) == 8 ? 2 * (size_t)NT : 64);
-  double* slots = reinterpret_cast<double*>(smem + off);   // [2][16][2]
-  const uint32_t Rbase = cm.rstart[me];
-  const double sigma = *d_sigma;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  cluster_sync_all();   // every CTA's shared memory is in place before remote access
-  auto each_block = [&](auto&& f) {
-    for (int lb = wid; lb < nbk; lb += NT / 32) {
-      const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
-      f(h, h.R - Rbase);
-    }
-  };
-  unsigned gen = 0;
-  // partial sums: CTA c writes its two values into slot c of every CTA, then
-  // the cluster barrier; each CTA adds the slots in rank order.
-  auto reduce = [&](T a, T b, double (&tot)[2]) {
-    double c0, c1;
-    cta_sum2<T>(a, b, stmp, c0, c1);
-    ++gen;
-    double* buf = slots + (gen & 1u) * 32;
-    if (threadIdx.x < CS) {   // warp 0 lanes all hold the CTA totals
-      const uint32_t dst = dsmem_map(smem_addr(buf + 2 * me), (uint32_t)threadIdx.x);
-      st_dsmem_f64(dst, c0);
-      st_dsmem_f64(dst + 8, c1);
-    }
-    cluster_sync_all();
-    double t0 = 0.0, t1 = 0.0;
-    for (int c = 0; c < CS; ++c) {
-      t0 += buf[2 * c];
-      t1 += buf[2 * c + 1];
-    }
-    tot[0] = t0;
-    tot[1] = t1;
-  };
-  {
-    T acc = T(0), zm = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) {
-        T am;
-        const T m = row_m<T, PC>(low[h.off + r], h, am);
-        const uint32_t i = h.R + r;
-        const uint32_t l = l0 + r;
-        const T b = bv[i];
-        zm += (m == T(0)) ? T(1) : T(0);
-        const T mi = m == T(0) ? T(0) : T(1) / m;
-        const T q = b * mi;
-        MV[l] = m; MI[l] = mi;
-        QL1[l] = q;
-        QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
-        acc += q * b;
-      }
-    });
-    double tot[2];
-    reduce(acc, zm, tot);
-    if (threadIdx.x == 0) {
-      init_state(S, tot[0], tot[1], tol, kmax, sigma);
-      s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
-      s_ibp = 1.0;
-    }
-    __syncthreads();
-  }
-  while (S.done != 2) {
-    const long long k = S.k;
-    const bool odd = (k & 1) != 0;
-    T* QLc = odd ? QL1 : QL0;          // q_k
-    T* QLp = odd ? QL0 : QL1;          // q_{k-1} -> q_{k+1}
-    T* DA = odd ? D1 : D0;             // d_{k-2}
-    T* DB = odd ? D0 : D1;             // d_{k-3} -> d_{k-1}
-    const uint32_t qbase = smem_addr(QLc);
-    const bool doC = S.pending != 0, doMV = S.done == 0;
-    const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
-    T acc = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      if (doC)
-        for (int r = lane; r < h.C; r += 32) {
-          const uint32_t l = l0 + r;
-          const T d = cq * QLp[l] + cd1 * DA[l] + cd2 * DB[l];
-          DB[l] = d;
-          X[l] += tau * d;
-        }
-      if (doMV) {
-        T xi[JM], hx[JM];
-        block_hv_cl<T, JM>(g, cm, CS, qbase, QLc + l0, low, h, xi, hx);
-#pragma unroll
-        for (int j = 0; j < JM; ++j) {
-          const int r = lane + 32 * j;
-          if (j < h.J && r < h.C) {
-            P[l0 + r] = hx[j];
-            acc += xi[j] * hx[j];
-          }
-        }
-      }
-    });
-    if (!doMV) break;                  // final pending d/x update done
-    double tot[2];
-    reduce(acc, T(0), tot);
-    if (threadIdx.x == 0) {
-      S.pending = 0;
-      S.alpha = tot[0] * s_ib * s_ib;
-      if (!isfinite(S.alpha)) { S.status = HS_NONFINITE; S.done = 2; }
-    }
-    __syncthreads();
-    if (S.done == 2) break;
-    const T c1 = (T)s_ib, c2 = (T)(S.alpha * s_ib), c3 = (T)(S.beta * s_ibp);
-    T acc2 = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) {
-        const uint32_t l = l0 + r;
-        const T q = P[l] * MI[l] * c1 - c2 * QLc[l] - c3 * QLp[l];
-        QLp[l] = q;
-        acc2 += MV[l] * q * q;
-      }
-    });
-    reduce(acc2, T(0), tot);
-    if (threadIdx.x == 0) {
-      double ib = s_ib;
-      givens_fast(S, tot[0], ib);
-      s_ibp = s_ib;
-      s_ib = ib;
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-  each_block([&](const Hdr& h, uint32_t l0) {
-    for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
-  });
-  if (me == 0 && threadIdx.x == 0) {
-    if (S.done != 2) S.done = 2;
-    *st = S;
-  }
-  cluster_sync_all();   // no CTA leaves while others may still read its shared memory
-}
-
 // Per-pass kernels (graph path, used when a cooperative launch is not
 // available): the same row passes, with last-CTA reductions.
 template <typename T, int PC>
@@ -1336,79 +1043,6 @@ static hs_status solve_smem_v(hs_handle* hd, const T* b, const MinresVecs& v, do
   return HS_OK;
 }
 
-// Cluster solve; HS_CUDA without a message when it does not apply.
-template <typename T, int PC, int JM, int NT>
-static hs_status solve_cluster_v(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
-                                 long long kmax, int CS) {
-  int* first = nullptr;
-  int rows_cap = 0, hdr_cap = 0;
-  hs_status st = smr_plan(hd, CS, &first, &rows_cap, &hdr_cap);
-  if (st != HS_OK) return st;
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, hd->device);
-  const size_t sm = cl_bytes<T>((int)hd->low.size(), hdr_cap, rows_cap, NT);
-  if (sm + sizeof(MinresState) + 64 > (size_t)optin) return HS_CUDA;
-  auto kern = k_minres_cluster<T, PC, JM, NT>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return HS_CUDA;
-  }
-  if (CS > 8 &&
-      cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-    cudaGetLastError();
-    return HS_CUDA;
-  }
-  std::vector<int> fh(CS + 1);
-  HS_CUDA_TRY(hd, cudaMemcpyAsync(fh.data(), first, sizeof(int) * (CS + 1), cudaMemcpyDeviceToHost,
-                                  hd->stream));
-  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
-  ClusterMap cm;
-  for (int c = 0; c < 17; ++c) cm.rstart[c] = (uint32_t)hd->n;
-  for (int c = 0; c < CS; ++c) cm.rstart[c] = fh[c] < (int)hd->blocks.size() ? hd->blocks[fh[c]].R : (uint32_t)hd->n;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(CS);
-  cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = hd->stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CS;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int nclusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)kern, &cfg) != cudaSuccess || nclusters < 1) {
-    cudaGetLastError();
-    return HS_CUDA;
-  }
-  Geo g = hd->geo();
-  const double* ds = hd->d_sigma;
-  T* xo = (T*)v.x;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, g, b, xo, hd->d_state, tol, kmax, ds,
-                                     (const int*)first, rows_cap, hdr_cap, cm, CS);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return HS_CUDA;
-  }
-  count_launches(1);
-  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
-                                  cudaMemcpyDeviceToHost, hd->stream));
-  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
-  return HS_OK;
-}
-
-// Cluster of 8 CTAs (16 when 8 do not hold the vectors), blocks of <= 96 rows.
-template <typename T, int PC>
-static hs_status solve_cluster(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
-                               long long kmax) {
-  if (hd->k > 8) return HS_CUDA;
-  hs_status st = solve_cluster_v<T, PC, 3, 1024>(hd, b, v, tol, kmax, 8);
-  if (st == HS_CUDA) st = solve_cluster_v<T, PC, 3, 1024>(hd, b, v, tol, kmax, 16);
-  return st;
-}
-
 // Blocks of at most 96 rows (k <= 8) take 3 rows per lane and 1024 threads;
 // larger blocks 8 rows per lane and 512 threads.
 template <typename T, int PC>
@@ -1513,21 +1147,6 @@ static bool force_graph() {
   return g_force_graph == 1;
 }
 
-// HS_MINRES_CLUSTER=1 selects the cluster form. It is opt-in: with FP64
-// vectors the 8 SMs of one cluster make the solve FP64-pipe-bound (about 2 FP64
-// operations per clock per SM on this part), and measured slower than the
-// grid-wide form, also when several realisations run side by side.
-static bool want_cluster() {
-  const char* e = getenv("HS_MINRES_CLUSTER");
-  return e && e[0] == '1';
-}
-
-// HS_MINRES_GRID=1 skips the cluster form (tests compare forms).
-static bool force_grid() {
-  const char* e = getenv("HS_MINRES_GRID");
-  return e && e[0] == '1';
-}
-
 // HS_MINRES_GLOBAL=1 skips the shared-memory-resident form (tests compare forms).
 static bool force_global() {
   const char* e = getenv("HS_MINRES_GLOBAL");
@@ -1541,9 +1160,7 @@ static hs_status solve_pc(hs_handle* hd, const T* b, T* x, double tol, long long
   hs_status st = ensure_ws<T>(hd, v);
   if (st != HS_OK) return st;
   st = HS_CUDA;
-  if (!force_graph() && !force_global() && !force_grid() && want_cluster())
-    st = solve_cluster<T, PC>(hd, b, v, tol, kmax);
-  if (st == HS_CUDA && !force_graph() && !force_global()) st = solve_smem<T, PC>(hd, b, v, tol, kmax);
+  if (!force_graph() && !force_global()) st = solve_smem<T, PC>(hd, b, v, tol, kmax);
   if (st == HS_CUDA && !force_graph()) st = solve_persist<T, PC>(hd, b, v, tol, kmax);
   if (st == HS_CUDA && (st = solve_graph<T, PC>(hd, b, v, tol, kmax)) != HS_OK) return st;
   if (st != HS_OK) return st;

@@ -127,19 +127,27 @@ __global__ void __launch_bounds__(TNA_THREADS) k_twist_noalloc(int L, long long 
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Device address of g_twist_scratch, looked up once per device.
+// Device address of g_twist_scratch. It is looked up again on every call made
+// outside a stream capture (a cudaDeviceReset reloads the module, and the
+// array may then live elsewhere); during a capture the address cached by the
+// last uncaptured call on this device is used.
 std::mutex g_mu;
 double* g_ptr[64] = {nullptr};
 
-hs_status scratch_for_current_device(double** out) {
+hs_status scratch_for_current_device(cudaStream_t s, double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return HS_CUDA;
   }
   if (dev < 0 || dev >= 64) return HS_BAD_ARG;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return HS_CUDA;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_ptr[dev]) {
     double* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_twist_scratch);
     if (e != cudaSuccess || !p) {
@@ -160,10 +168,10 @@ extern "C" hs_status hs_twist_noalloc(int L, const double* psi_dev, int K, doubl
   if (K < 1 || K > TNA_K_MAX) return HS_BAD_ARG;   // the scratch holds 8 vectors
   if (!psi_dev || !z_dev) return HS_BAD_ARG;
   double* scratch = nullptr;
-  const hs_status st = scratch_for_current_device(&scratch);
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const hs_status st = scratch_for_current_device(s, &scratch);
   if (st != HS_OK) return st;
   const long long n = (long long)hs::binom(L, L / 2);
-  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   // the arrival counter must start at zero (a previous call leaves it at zero
   // unless it was interrupted)
   if (cudaMemsetAsync(scratch + TNA_PART, 0, sizeof(double), s) != cudaSuccess) {

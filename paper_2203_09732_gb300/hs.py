@@ -42,7 +42,8 @@ class LanczosInfo(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("converged", ctypes.c_int),
                 ("minres_iters", ctypes.c_longlong), ("sweeps", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("max_resid", ctypes.c_double),
-                ("seconds_solve", ctypes.c_double), ("seconds_total", ctypes.c_double)]
+                ("seconds_solve", ctypes.c_double), ("seconds_total", ctypes.c_double),
+                ("unconverged_solves", ctypes.c_int), ("pad", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -135,3 +135,43 @@ def test_concurrent_handles_reuse_pool_memory():
     for t in th:
         t.join()
     assert not errors, errors
+
+
+@pytest.mark.parametrize("form", [None, "HS_MINRES_GLOBAL"])
+def test_sm_budget_changed_while_solving(l14, form, monkeypatch):
+    """Another host thread changes the handle's SM share (4 -> 16 -> 0 = all)
+    while hs_lanczos_eigs runs: each MINRES solve reads the share when it
+    starts, and the shared-memory form re-plans its per-CTA rows for the new
+    grid. The eigenpairs must still match dense eigh."""
+    import threading
+    import time
+    hs = need_gpu()
+    if form:
+        monkeypatch.setenv(form, "1")
+    L, hv, H, st, w, V = l14
+    sigma = 0.5 * (w[0] + w[-1])
+    K = 6
+    idx = np.lexsort((w, np.abs(w - sigma)))[:K]
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        c.set_sm_budget(4)
+        done = threading.Event()
+        seen = []
+
+        def changer():
+            for nsm in (16, 0, 4, 16, 0):
+                if done.wait(0.05):
+                    break
+                c.set_sm_budget(nsm)
+                seen.append(nsm)
+
+        t = threading.Thread(target=changer)
+        t.start()
+        try:
+            ev, vecs, res, info = c.eigs(K, seed=9)
+        finally:
+            done.set()
+            t.join()
+    assert seen, "the share never changed during the solve"
+    assert np.abs(ev - w[idx]).max() < 1e-10
+    ov = np.abs(np.einsum("in,ni->i", vecs.cpu().numpy(), V[:, idx]))
+    assert (ov > 1 - 1e-8).all() and info["converged"] == K

@@ -95,27 +95,3 @@ def test_matvec_sampled_rows_large(L, dtype):
         mag = abs(d * xs[i]) + sum(abs(v * xs[j]) for j, v in off)
         tol = (1e-14 if dtype == "f64" else (L + 4) * 2.0 ** -23) * mag + 1e-300
         assert abs(y[i] - ref) <= tol, (i, y[i], ref)
-
-
-@pytest.mark.parametrize("L", [22, 24])
-@pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_staged_matvec_matches_gather_form(L, dtype, monkeypatch):
-    """The bulk-copy staged H x (blocks of C(10, w) rows) against the gather
-    form: same per-row arithmetic, read from shared memory instead of
-    global memory, so the results agree exactly."""
-    hs = need_gpu()
-    h = inputs.disorder(L, 3.0, 9)
-    tdt = torch.float64 if dtype == "f64" else torch.float32
-    with hs.Chain(L, h, sigma=0.2) as c:
-        x = torch.randn(c.n, generator=torch.Generator().manual_seed(1), dtype=torch.float64).to(tdt).cuda()
-        y0 = c.matvec(x, shifted=True)
-        monkeypatch.setenv("HS_HV_TMA", "1")
-        y1 = c.matvec(x, shifted=True)
-        y2 = c.matvec(x, shifted=False)
-        monkeypatch.delenv("HS_HV_TMA")
-        y3 = c.matvec(x, shifted=False)
-        torch.cuda.synchronize()
-    scale = float(y0.abs().max())
-    tol = (1e-14 if dtype == "f64" else (L + 4) * 2.0 ** -23) * scale * L
-    assert float((y1 - y0).abs().max()) <= tol
-    assert float((y2 - y3).abs().max()) <= tol

@@ -133,9 +133,6 @@ def test_barrier_timeout_reports_status(monkeypatch):
     L = 16
     hv, H, diag, A, sigma = _sys(L, seed=3)
     b = to_dev(inputs.gaussian(A.shape[0], 1))
-    # the grid-wide forms wait in software (the cluster form uses the hardware
-    # cluster barrier, which has no timeout to test)
-    monkeypatch.setenv("HS_MINRES_GRID", "1")
     with hs.Chain(L, hv, sigma=sigma) as c:
         monkeypatch.setenv("HS_BARRIER_LIMIT", "0")
         with pytest.raises(hs.HSError) as e:
@@ -147,11 +144,11 @@ def test_barrier_timeout_reports_status(monkeypatch):
     assert np.linalg.norm(A @ x.cpu().numpy() - b.cpu().numpy()) < 1e-6 * np.linalg.norm(b.cpu().numpy())
 
 
-@pytest.mark.parametrize("form", ["HS_MINRES_GRAPH", "HS_MINRES_CLUSTER", "HS_MINRES_GLOBAL"])
+@pytest.mark.parametrize("form", ["HS_MINRES_GRAPH", "HS_MINRES_GLOBAL"])
 @pytest.mark.parametrize("L", [12, 16])
 def test_solver_forms_agree(L, form, monkeypatch):
-    """Every solver form (per-pass kernels under a CUDA graph, the cluster
-    form, the global-memory persistent form) against the default
+    """Every solver form (per-pass kernels under a CUDA graph, the
+    global-memory persistent form) against the default
     shared-memory persistent form: the same row passes, so iteration counts
     agree to rounding drift and both solutions meet the tolerance."""
     hs = need_gpu()
@@ -184,24 +181,3 @@ with hs.Chain({L}, hv, sigma={sigma!r}) as c:
     bb = b.cpu().numpy()
     for x in (x2, x1.cpu().numpy()):
         assert np.linalg.norm(A @ x - bb) <= 1e-7 * np.linalg.norm(bb)
-
-
-@pytest.mark.parametrize("L", [8, 12, 16])
-def test_cluster_form_iterates(L, monkeypatch):
-    """The cluster form (DSMEM gathers, hardware cluster barrier) against the
-    oracle's Algorithm 2 iterates."""
-    hs = need_gpu()
-    monkeypatch.setenv("HS_MINRES_CLUSTER", "1")
-    hv, H, diag, A, sigma = _sys(L, seed=4)
-    b = inputs.gaussian(A.shape[0], 13)
-    M = hamiltonian.precond_diag(H, diag, sigma, "row")
-    for k in (3, 7):
-        xr, kr, phir = minres.pminres(A, b, 1.0 / M, kmax=k, tol=0.0)
-        with hs.Chain(L, hv, sigma=sigma) as c:
-            x, info = c.minres(to_dev(b), tol=0.0, kmax=k, allow_not_converged=True)
-        assert info["iters"] == k
-        spread = M.max() / M.min()
-        assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-12 * spread * np.linalg.norm(xr)
-    with hs.Chain(L, hv, sigma=sigma) as c:
-        x, info = c.minres(to_dev(b), tol=1e-11)
-    assert np.linalg.norm(A @ x.cpu().numpy() - b) <= 1e-8 * np.linalg.norm(b)

@@ -12,12 +12,15 @@ from tests.gpu_util import need_gpu, to_dev, torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("L", [12, 16])
-def test_matches_hs_twist_on_two_calls(L):
+@pytest.mark.parametrize("L,ka,kb", [(12, 3, 5), (16, 3, 5), (24, 8, 2)])
+def test_matches_hs_twist_on_two_calls(L, ka, kb):
+    """L = 24 (n = 2.7M) fills the 256-CTA grid, so the last-CTA reduction
+    adds 256 partial rows and threads unrank starting ranks in the millions;
+    K = 8 is the most vectors the scratch holds."""
     hs = need_gpu()
     n = inputs.dim(L)
-    psi_a = to_dev(inputs.gaussian(n, 31, count=3))
-    psi_b = to_dev(inputs.gaussian(n, 32, count=5))
+    psi_a = to_dev(inputs.gaussian(n, 31, count=ka))
+    psi_b = to_dev(inputs.gaussian(n, 32, count=kb))
     with hs.Chain(L, np.zeros(L), sigma=0.0) as c:
         ref_a = c.twist(psi_a)
         ref_b = c.twist(psi_b)
