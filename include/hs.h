@@ -65,7 +65,15 @@ typedef struct {
   double phi;          /* last |phi_k| / beta_1 of the last inner solve           */
   double resid_minv;   /* final ||b - (H - sigma) x||_{M^-1} / ||b||_{M^-1}, FP64 */
   double resid_2;      /* final ||b - (H - sigma) x||_2 / ||b||_2, FP64          */
+  int form;            /* solver form of the (last inner) solve: HS_FORM_*        */
+  int pad;
 } hs_minres_info;
+
+/* Solver forms (all run the same recurrence of Algorithm 2): vectors resident
+ * in shared memory (chains up to L = 20 in FP64, 22 in FP32); superblock
+ * passes (from L = 24 on); one persistent cooperative kernel with vectors in
+ * global memory; per-pass kernels replayed from a CUDA graph. */
+enum { HS_FORM_SMEM = 1, HS_FORM_SUPERBLOCK = 2, HS_FORM_PERSISTENT = 3, HS_FORM_GRAPH = 4 };
 
 typedef struct {
   int steps;           /* Lanczos steps taken (k at exit)                         */
@@ -76,8 +84,10 @@ typedef struct {
   double max_resid;    /* max_i ||H psi_i - E_i psi_i||_2 (FP64, certified)       */
   double seconds_solve;   /* host wall time inside the MINRES solves             */
   double seconds_total;   /* host wall time of the whole call                    */
+  double seconds_ritz;    /* host wall time of the Ritz extraction and the FP64  */
+                          /* certification of the K pairs (part of the total)    */
   int unconverged_solves; /* MINRES solves that stopped at their iteration cap   */
-                          /* (50 n) before minres_tol; the step still used them  */
+                          /* before minres_tol; the step still used them         */
   int pad;
 } hs_lanczos_info;
 
@@ -162,7 +172,11 @@ hs_status hs_minres_f32(hs_handle* hd, const float* b_dev, float* x_dev, double 
  *   every wanted Ritz pair has beta_{k+1} |y_{k,i}| <= tol |theta_i|;
  *   seed: SplitMix64 stream of the start vector (entries uniform on [-1, 1));
  *   v0_dev: optional FP64 start vector (overrides seed); mixed, pc, inner_tol:
- *   as hs_minres, with MINRES tolerance minres_tol.
+ *   as hs_minres, with MINRES tolerance minres_tol; minres_kmax: iteration cap
+ *   of each MINRES solve, all refinement sweeps together (<= 0: 50 n). A solve
+ *   that reaches the cap still feeds its iterate into the step and is counted
+ *   in info->unconverged_solves (a capped run measures the cost of every part
+ *   of the pipeline on problems whose full solve takes too long).
  * Outputs: evals_host[K] ordered by |E - sigma| (ties by E), E_i the Rayleigh
  * quotient of psi_i; evecs_dev (K x n FP64, vector i at evecs_dev + i n; may be
  * NULL); resid_host[K] = ||H psi_i - E_i psi_i||_2 (may be NULL).
@@ -170,8 +184,8 @@ hs_status hs_minres_f32(hs_handle* hd, const float* b_dev, float* x_dev, double 
 hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol,
                           unsigned long long seed, const double* v0_dev, int mixed,
                           hs_precond pc, double minres_tol, double inner_tol,
-                          double* evals_host, double* evecs_dev, double* resid_host,
-                          hs_lanczos_info* info);
+                          long long minres_kmax, double* evals_host, double* evecs_dev,
+                          double* resid_host, hs_lanczos_info* info);
 
 /* End-to-end convenience call with host buffers only: creates a handle on the
  * current device (its own stream; persistent solves limited to sm_budget SMs,
@@ -180,9 +194,9 @@ hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol,
  * NULL) and frees everything. sigma NaN = midpoint. */
 hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_max,
                        double tol, unsigned long long seed, int mixed, hs_precond pc,
-                       double minres_tol, double inner_tol, int sm_budget,
-                       double* evals_host, double* evecs_host, double* resid_host,
-                       double* z_host, hs_lanczos_info* info);
+                       double minres_tol, double inner_tol, long long minres_kmax,
+                       int sm_budget, double* evals_host, double* evecs_host,
+                       double* resid_host, double* z_host, hs_lanczos_info* info);
 
 /* Twist overlap z_i = <psi_i| U_twist |psi_i>, U_twist = exp[i 2pi/L sum_j j Sz_j]
  * (Sec. III), for K real FP64 vectors psi_dev + i n (not normalised by the

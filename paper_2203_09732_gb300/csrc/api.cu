@@ -334,7 +334,13 @@ hs_status hs_create(int L, const double* h_host, double sigma, void* cuda_stream
       for (int c = 0; c < W; ++c) bt[a * W + c] = binom(a, c);
     if ((st = upload(hd, &hd->d_binom, bt)) != HS_OK) return bail(st);
   }
-  if (L >= 22 && (st = sb_setup(hd)) != HS_OK) return bail(st);
+  // superblock plans for long chains; HS_SB_PLANS=1 builds them for any L
+  // whose windows apply (tests of the superblock forms on small chains)
+  {
+    const char* e = getenv("HS_SB_PLANS");
+    const bool plans = L >= 22 || (e && e[0] == '1');
+    if (plans && (st = sb_setup(hd)) != HS_OK) return bail(st);
+  }
   if ((st = dev_alloc(hd, (void**)&hd->d_sigma, sizeof(double))) != HS_OK) return bail(st);
   if ((st = ensure_reduce(hd)) != HS_OK) return bail(st);
   if (std::isnan(sigma)) {
@@ -366,6 +372,8 @@ void hs_free(hs_handle* hd) {
   dev_free(hd, hd->d_state);
   dev_free(hd, hd->lz);
   dev_free(hd, hd->d_smr_first);
+  sb_graphs_release(hd, 0);
+  sb_graphs_release(hd, 1);
   sb_release(hd);
   host_pinned_put(hd->h_pinned, PINNED_RED_BYTES);
   host_pinned_put(hd->h_state, sizeof(MinresState));

@@ -147,6 +147,11 @@ struct hs_handle {
 
   // superblock H x plans (hv_sb.cu): [0] FP32, [1] FP64; null where not built
   void* sb_plan[2] = {nullptr, nullptr};
+  // superblock MINRES chunk graphs (minres_sb.cu), [precision][preconditioner],
+  // with the grids (pass A, pass B) and the workspace they were captured for
+  cudaGraphExec_t sbgraph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  int sbgraph_key[2][3][2] = {};
+  void* sbgraph_ws[2] = {nullptr, nullptr};
 
   // Lanczos workspace
   double* lz = nullptr; size_t lz_vectors = 0;
@@ -194,6 +199,10 @@ hs_status launch_diag(hs_handle* hd, double* diag, hs_precond pc, double* minv);
 // FP64 r = b - (H - sigma) x; returns sum r^2/M and sum r^2 and the same for b.
 hs_status resid64(hs_handle* hd, const double* b, const double* x, double* r, hs_precond pc,
                   double sums_out[4]);
+
+// minres_sb.cu: destroy the cached superblock MINRES graphs of precision ti
+// (0 FP32, 1 FP64), e.g. before the workspace they point into is freed
+void sb_graphs_release(hs_handle* hd, int ti);
 
 // minres.cu -----------------------------------------------------------------
 hs_status minres_solve64(hs_handle* hd, const double* b, double* x, double tol, long long kmax,

@@ -160,7 +160,8 @@ extern "C" hs_status hs_extremal(hs_handle* hd, int max_steps, double tol, doubl
 extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol,
                                      unsigned long long seed, const double* v0_dev, int mixed,
                                      hs_precond pc, double minres_tol, double inner_tol,
-                                     double* evals_host, double* evecs_dev, double* resid_host,
+                                     long long minres_kmax, double* evals_host,
+                                     double* evecs_dev, double* resid_host,
                                      hs_lanczos_info* info) {
   using clk = std::chrono::steady_clock;
   const auto t0 = clk::now();
@@ -169,6 +170,7 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
   if (K < 1 || K > n || !evals_host) return fail(hd, HS_BAD_ARG, "hs_lanczos_eigs: bad K or output");
   if (!(tol > 0)) tol = 1e-10;
   if (!(minres_tol > 0)) minres_tol = 1e-12;
+  const long long kcap = minres_kmax > 0 ? minres_kmax : 50 * n;
   int m = m_max > 0 ? m_max : std::max(130, 3 * K + 30);
   m = (int)std::min<long long>(m, n);
   if (m < K) m = K;
@@ -199,8 +201,8 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
     double* vk = V + (size_t)k * n;
     const auto ts = clk::now();
     std::memset(&mi, 0, sizeof(mi));
-    if (mixed) st = minres_mixed(hd, vk, x, minres_tol, 50 * n, pc, inner_tol > 0 ? inner_tol : 1e-5, &mi);
-    else st = minres_solve64(hd, vk, x, minres_tol, 50 * n, pc, &mi);
+    if (mixed) st = minres_mixed(hd, vk, x, minres_tol, kcap, pc, inner_tol > 0 ? inner_tol : 1e-5, &mi);
+    else st = minres_solve64(hd, vk, x, minres_tol, kcap, pc, &mi);
     solve_s += std::chrono::duration<double>(clk::now() - ts).count();
     if (info) { info->minres_iters += mi.iters; info->sweeps += mixed ? mi.sweeps : 1; }
     if (st != HS_OK && st != HS_NOT_CONVERGED) return st;
@@ -248,6 +250,7 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
     beta_k = bn;
   }
   // Ritz pairs: K largest |theta|, then ordered by |E - sigma| (ties by E)
+  const auto tr = clk::now();
   const int kk = steps;
   std::vector<int> ord(kk);
   std::iota(ord.begin(), ord.end(), 0);
@@ -291,6 +294,7 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
     info->max_resid = max_res;
     info->seconds_solve = solve_s;
     info->seconds_total = std::chrono::duration<double>(clk::now() - t0).count();
+    info->seconds_ritz = std::chrono::duration<double>(clk::now() - tr).count();
   }
   if (nconv < K) {
     hd->err = "Lanczos reached m_max before all wanted pairs converged";
@@ -301,9 +305,9 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
 
 extern "C" hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_max,
                                   double tol, unsigned long long seed, int mixed, hs_precond pc,
-                                  double minres_tol, double inner_tol, int sm_budget,
-                                  double* evals_host, double* evecs_host, double* resid_host,
-                                  double* z_host, hs_lanczos_info* info) {
+                                  double minres_tol, double inner_tol, long long minres_kmax,
+                                  int sm_budget, double* evals_host, double* evecs_host,
+                                  double* resid_host, double* z_host, hs_lanczos_info* info) {
   cudaStream_t s;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
@@ -320,7 +324,7 @@ extern "C" hs_status hs_eigs_host(int L, const double* h_host, double sigma, int
     return HS_OOM;
   }
   st = hs_lanczos_eigs(hd, K, m_max, tol, seed, nullptr, mixed, pc, minres_tol, inner_tol,
-                       evals_host, ev, resid_host, info);
+                       minres_kmax, evals_host, ev, resid_host, info);
   if ((st == HS_OK || st == HS_NOT_CONVERGED) && z_host) {
     hs_status s2 = hs_twist(hd, ev, K, z_host);
     if (s2 != HS_OK) st = s2;

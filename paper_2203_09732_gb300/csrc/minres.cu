@@ -17,13 +17,10 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include "minres_scalar.cuh"
 #include "rows.cuh"
 
 namespace hs {
-
-struct MinresVecs {
-  void* q0; void* q1; void* d0; void* d1; void* p; void* x;
-};
 
 // ---------------------------------------------------------------------------
 // Row passes shared by the per-pass kernels and the persistent kernel. Each
@@ -112,50 +109,6 @@ __device__ __forceinline__ void rows_B(const Geo& g, const RowSmem<T>& s, double
       acc += m * q * q;
     }
   });
-}
-
-// Scalar part of pass B (Givens rotation of Algorithm 2), on one thread.
-__device__ __forceinline__ void givens_update(MinresState& S, double sumsq) {
-  const double bn = sumsq >= 0.0 ? sqrt(sumsq) : NAN;        // beta_{k+1}
-  const double a = S.alpha, bk = S.beta;
-  const double cp = S.c_prev, sp = S.s_prev, dh = S.delta_hat, eps = S.eps;
-  const double delta = cp * dh + sp * a;                     // delta_k
-  const double gh = -sp * dh + cp * a;                       // hat gamma_k
-  const double eps_n = sp * bn;                              // epsilon_{k+1}
-  const double dh_n = cp * bn;                               // hat delta_{k+1}
-  const double gamma = sqrt(gh * gh + bn * bn);              // gamma_k
-  if (!isfinite(bn) || !isfinite(gamma)) {
-    S.status = HS_NONFINITE; S.done = 2; S.pending = 0;
-    return;
-  }
-  if (gamma == 0.0) {
-    S.status = HS_BREAKDOWN; S.done = 2; S.pending = 0;
-    return;
-  }
-  const double c = gh / gamma, sn = bn / gamma;              // c_k, s_k
-  const double tau = c * S.phi;                              // tau_k
-  const double phi = -sn * S.phi;                            // phi_k
-  S.cq = 1.0 / (bk * gamma);
-  S.cd1 = -delta / gamma;
-  S.cd2 = -eps / gamma;
-  S.tau = tau;
-  S.pending = 1;
-  S.beta_prev = bk; S.beta = bn;
-  S.delta_hat = dh_n; S.eps = eps_n;
-  S.c_prev = c; S.s_prev = sn; S.phi = phi;
-  S.k = S.k + 1;
-  if (fabs(phi) < S.tol_abs || bn == 0.0 || S.k > S.kmax) S.done = 1;
-}
-
-__device__ __forceinline__ void init_state(MinresState& S, double sumsq, double zero_m,
-                                           double tol, long long kmax, double sigma) {
-  const double beta1 = sumsq >= 0.0 ? sqrt(sumsq) : NAN;     // NaN/Inf propagate
-  S.beta_prev = 1.0; S.beta = beta1; S.beta1 = beta1; S.alpha = 0.0;
-  S.c_prev = 1.0; S.s_prev = 0.0; S.delta_hat = 0.0; S.eps = 0.0; S.phi = beta1;
-  S.tol_abs = tol * beta1; S.cq = S.cd1 = S.cd2 = S.tau = 0.0; S.sigma = sigma;
-  S.k = 1; S.kmax = kmax; S.pending = 0; S.pad = 0;
-  S.status = zero_m > 0 ? HS_BAD_ARG : (isfinite(beta1) ? HS_OK : HS_NONFINITE);
-  S.done = (S.status != HS_OK || beta1 == 0.0 || kmax <= 0 || beta1 < S.tol_abs) ? 2 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -852,6 +805,7 @@ static hs_status ensure_ws(hs_handle* hd, MinresVecs& v) {
     cudaGraphExec_t* gr = sizeof(T) == 8 ? hd->graph64 : hd->graph32;
     for (int i = 0; i < 3; ++i)
       if (gr[i]) { cudaGraphExecDestroy(gr[i]); gr[i] = nullptr; }
+    sb_graphs_release(hd, sizeof(T) == 8 ? 1 : 0);
     if (dev_alloc(hd, ws, need) != HS_OK)
       return fail(hd, HS_OOM, "MINRES workspace allocation failed");
     *wsb = need;
@@ -1153,6 +1107,24 @@ static bool force_global() {
   return e && e[0] == '1';
 }
 
+// The superblock form (minres_sb.cu) takes the solves the shared-memory form
+// cannot hold, from L = 24 on. HS_MINRES_SB=0 turns it off; =1 makes it the
+// first choice wherever a superblock plan exists (tests compare forms).
+static int sb_choice(const hs_handle* hd) {
+  const char* e = getenv("HS_MINRES_SB");
+  if (e) return e[0] == '1' ? 2 : 0;
+  return hd->L >= 24 ? 1 : 0;
+}
+
+template <typename T, int PC>
+static hs_status try_sb(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
+                        long long kmax) {
+  bool used = false;
+  const hs_status s2 = minres_solve_sb(hd, b, v, sizeof(T) == 8 ? HS_F64 : HS_F32, PC, tol,
+                                       kmax, &used);
+  return (used || s2 != HS_OK) ? s2 : HS_CUDA;
+}
+
 template <typename T, int PC>
 static hs_status solve_pc(hs_handle* hd, const T* b, T* x, double tol, long long kmax,
                           hs_minres_info* info) {
@@ -1160,9 +1132,22 @@ static hs_status solve_pc(hs_handle* hd, const T* b, T* x, double tol, long long
   hs_status st = ensure_ws<T>(hd, v);
   if (st != HS_OK) return st;
   st = HS_CUDA;
-  if (!force_graph() && !force_global()) st = solve_smem<T, PC>(hd, b, v, tol, kmax);
-  if (st == HS_CUDA && !force_graph()) st = solve_persist<T, PC>(hd, b, v, tol, kmax);
-  if (st == HS_CUDA && (st = solve_graph<T, PC>(hd, b, v, tol, kmax)) != HS_OK) return st;
+  int form = 0;
+  const int sbc = sb_choice(hd);
+  if (sbc == 2 && (st = try_sb<T, PC>(hd, b, v, tol, kmax)) != HS_CUDA) form = HS_FORM_SUPERBLOCK;
+  if (st == HS_CUDA && !force_graph() && !force_global() &&
+      (st = solve_smem<T, PC>(hd, b, v, tol, kmax)) != HS_CUDA)
+    form = HS_FORM_SMEM;
+  if (st == HS_CUDA && !force_graph() && sbc == 1 &&
+      (st = try_sb<T, PC>(hd, b, v, tol, kmax)) != HS_CUDA)
+    form = HS_FORM_SUPERBLOCK;
+  if (st == HS_CUDA && !force_graph() &&
+      (st = solve_persist<T, PC>(hd, b, v, tol, kmax)) != HS_CUDA)
+    form = HS_FORM_PERSISTENT;
+  if (st == HS_CUDA) {
+    form = HS_FORM_GRAPH;
+    if ((st = solve_graph<T, PC>(hd, b, v, tol, kmax)) != HS_OK) return st;
+  }
   if (st != HS_OK) return st;
   const MinresState S = *hd->h_state;
   HS_CUDA_TRY(hd, cudaMemcpyAsync(x, v.x, sizeof(T) * hd->n, cudaMemcpyDeviceToDevice,
@@ -1174,6 +1159,7 @@ static hs_status solve_pc(hs_handle* hd, const T* b, T* x, double tol, long long
     info->iters += S.k - 1;
     info->phi = S.beta1 > 0 ? std::fabs(S.phi) / S.beta1 : 0.0;
     info->status = out;
+    info->form = form;
   }
   if (out != HS_OK && out != HS_NOT_CONVERGED)
     return fail(hd, out, out == HS_BREAKDOWN ? "MINRES breakdown (gamma_k = 0)"
@@ -1247,7 +1233,7 @@ hs_status minres_mixed(hs_handle* hd, const double* b, double* x, double tol, lo
     st = minres_solve32(hd, r32, dx32, itol, left, pc, &in);
     if (st != HS_OK && st != HS_NOT_CONVERGED) return st;
     left -= in.iters;
-    if (info) { info->iters += in.iters; info->phi = in.phi; }
+    if (info) { info->iters += in.iters; info->phi = in.phi; info->form = in.form; }
     ++sweeps;
     // minres_solve32 used ws32; the FP32 solution was copied to dx32
     if ((st = vaxpy_f32_to_f64(hd, rn, dx32, x, n)) != HS_OK) return st;

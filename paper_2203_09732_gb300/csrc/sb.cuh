@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 namespace hs {
@@ -401,10 +402,12 @@ struct Lane {
 
 // Phase 2: the rows of one sub-block for one lane (r = lane + 32 j); shared
 // memory only, then one coalesced store. A lane past the last row repeats row
-// C - 1 and does not store.
+// C - 1 and does not store. Returns the lane's sum of x_i y_i over its rows
+// (alpha_k of Algorithm 2 when x = q_k).
 template <typename T>
-__host__ __device__ __forceinline__ void sb_lane(const Lane<T>& c, int lane) {
+__host__ __device__ __forceinline__ T sb_lane(const Lane<T>& c, int lane) {
   const int J = (c.C + 31) >> 5;
+  T dot = T(0);
 #pragma unroll
   for (int j = 0; j < JMAX; ++j) {
     if (j >= J) break;
@@ -432,8 +435,50 @@ __host__ __device__ __forceinline__ void sb_lane(const Lane<T>& c, int lane) {
       d = c.dlow[r] + c.uni + (0.5 - 0.5 * (double)(x0 + x1));
     else
       d = e.dlow_f + c.uni + (0.5f - 0.5f * (float)(x0 + x1));
-    if (valid) sb_st(c.yg + r, d * xi + T(0.5) * a);
+    const T yv = d * xi + T(0.5) * a;
+    if (valid) {
+      sb_st(c.yg + r, yv);
+      dot += xi * yv;
+    }
   }
+  return dot;
+}
+
+// Per-row quantities of one sub-block without its neighbours (the MINRES
+// passes that need the preconditioner M but no product): a_ii - sigma and the
+// number of antiparallel bonds naf (sum_{k != i} a_ik^2 = naf / 4), with the
+// same terms and the same order of additions as sb_lane's diagonal.
+template <typename T>
+struct RowCtx {
+  const Low16* low;      // low table, class w slice
+  const double* dlow;    // FP64 low terms, class w slice
+  T uni;                 // dmid + dT - sigma +- 1/4 for bond (KS-1, KS)
+  uint32_t mbit0, ttop;
+  int nfix;              // antiparallel mid bonds + bond (KS-1, KS) + high bonds
+  int C;                 // rows of the sub-block
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ T sb_diag(const RowCtx<T>& c, int r, int& naf) {
+  const Low16 e = c.low[r];
+  const uint32_t code = (e.meta >> 20) & 3u;
+  const uint32_t x0 = (code & 1u) ^ c.mbit0;
+  const uint32_t x1 = (code >> 1) ^ c.ttop;
+  naf = (int)((e.meta >> 16) & 0xFu) + c.nfix + (int)(x0 + x1);
+  if constexpr (sizeof(T) == 8)
+    return c.dlow[r] + c.uni + (0.5 - 0.5 * (double)(x0 + x1));
+  else
+    return e.dlow_f + c.uni + (0.5f - 0.5f * (float)(x0 + x1));
+}
+
+// M_ii of preconditioner PC (0 identity, 1 Jacobi |a_ii - sigma|, 2 row norm
+// sqrt((a_ii - sigma)^2 + naf / 4)), Sec. II.
+template <int PC, typename T>
+__host__ __device__ __forceinline__ T sb_precond(T am, int naf) {
+  if (PC == 0) return T(1);
+  if (PC == 1) return am < T(0) ? -am : am;
+  if constexpr (sizeof(T) == 8) return sqrt(am * am + 0.25 * (double)naf);
+  else return sqrtf(am * am + 0.25f * (float)naf);
 }
 
 }  // namespace sb

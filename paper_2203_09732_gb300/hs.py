@@ -21,6 +21,7 @@ STATUS_NAMES = ["HS_OK", "HS_BAD_ARG", "HS_OOM", "HS_CUDA", "HS_NOT_CONVERGED", 
                 "HS_NONFINITE", "HS_TIMEOUT"]
 F32, F64 = 0, 1
 PRECOND = {"id": 0, "jacobi": 1, "row": 2}
+FORM_SMEM, FORM_SUPERBLOCK, FORM_PERSISTENT, FORM_GRAPH = 1, 2, 3, 4
 
 # every symbol include/hs.h declares
 SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "hs_set_sigma",
@@ -32,7 +33,7 @@ SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "h
 class MinresInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_longlong), ("sweeps", ctypes.c_int), ("status", ctypes.c_int),
                 ("phi", ctypes.c_double), ("resid_minv", ctypes.c_double),
-                ("resid_2", ctypes.c_double)]
+                ("resid_2", ctypes.c_double), ("form", ctypes.c_int), ("pad", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -43,6 +44,7 @@ class LanczosInfo(ctypes.Structure):
                 ("minres_iters", ctypes.c_longlong), ("sweeps", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("max_resid", ctypes.c_double),
                 ("seconds_solve", ctypes.c_double), ("seconds_total", ctypes.c_double),
+                ("seconds_ritz", ctypes.c_double),
                 ("unconverged_solves", ctypes.c_int), ("pad", ctypes.c_int)]
 
     def as_dict(self):
@@ -87,12 +89,13 @@ def load(path=LIB_PATH):
         "hs_minres_f32": ([H, c_vp, c_vp, ctypes.c_double, ctypes.c_longlong, ctypes.c_int,
                            ctypes.POINTER(MinresInfo)], ctypes.c_int),
         "hs_lanczos_eigs": ([H, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_ulonglong, c_vp,
-                             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, c_dp, c_vp,
-                             c_dp, ctypes.POINTER(LanczosInfo)], ctypes.c_int),
+                             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_longlong, c_dp, c_vp, c_dp, ctypes.POINTER(LanczosInfo)],
+                            ctypes.c_int),
         "hs_eigs_host": ([ctypes.c_int, c_dp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                           ctypes.c_double, ctypes.c_ulonglong, ctypes.c_int, ctypes.c_int,
-                          ctypes.c_double, ctypes.c_double, ctypes.c_int, c_dp, c_dp, c_dp, c_dp,
-                          ctypes.POINTER(LanczosInfo)], ctypes.c_int),
+                          ctypes.c_double, ctypes.c_double, ctypes.c_longlong, ctypes.c_int, c_dp,
+                          c_dp, c_dp, c_dp, ctypes.POINTER(LanczosInfo)], ctypes.c_int),
         "hs_twist": ([H, c_vp, ctypes.c_int, c_dp], ctypes.c_int),
         "hs_tridiag_eig": ([ctypes.c_int, c_dp, c_dp, c_dp, c_dp], ctypes.c_int),
         "hs_kernel_launches": ([], ctypes.c_ulonglong),
@@ -279,15 +282,16 @@ class Chain:
         return x, info.as_dict()
 
     def eigs(self, K, m_max=0, tol=1e-10, seed=0, v0=None, mixed=False, precond="row",
-             minres_tol=1e-12, inner_tol=1e-5, vectors=True, allow_not_converged=False):
+             minres_tol=1e-12, inner_tol=1e-5, minres_kmax=0, vectors=True,
+             allow_not_converged=False):
         t = self.torch
         ev = np.zeros(K)
         res = np.zeros(K)
         vecs = t.empty((K, self.n), dtype=t.float64, device=self.device) if vectors else None
         info = LanczosInfo()
         st = self._lib.hs_lanczos_eigs(self._hd, K, m_max, tol, seed, _ptr(v0), int(mixed),
-                                       PRECOND[precond], minres_tol, inner_tol, _dp(ev), _ptr(vecs),
-                                       _dp(res), ctypes.byref(info))
+                                       PRECOND[precond], minres_tol, inner_tol, int(minres_kmax),
+                                       _dp(ev), _ptr(vecs), _dp(res), ctypes.byref(info))
         if not (allow_not_converged and st == HS_NOT_CONVERGED):
             self._check(st, "hs_lanczos_eigs")
         return ev, vecs, res, info.as_dict()
@@ -304,19 +308,26 @@ class Chain:
 
 
 def eigs_host(L, h, K, sigma=float("nan"), m_max=0, tol=1e-10, seed=0, mixed=True, precond="row",
-              minres_tol=1e-12, inner_tol=1e-5, vectors=True, twist=True, sm_budget=0):
-    """End-to-end call with host (numpy) buffers only: hs_eigs_host."""
+              minres_tol=1e-12, inner_tol=1e-5, minres_kmax=0, vectors=True, twist=True,
+              sm_budget=0, out=None):
+    """End-to-end call with host (numpy) buffers only: hs_eigs_host. `out`
+    may supply the (K, n) float64 eigenvector buffer (e.g. pinned memory)."""
     lib = load()
     hh = np.ascontiguousarray(h, dtype=np.float64)
     n = math.comb(L, L // 2)
     ev = np.zeros(K)
     res = np.zeros(K)
-    vec = np.zeros((K, n)) if vectors else None
+    if vectors:
+        vec = out if out is not None else np.zeros((K, n))
+        if vec.shape != (K, n) or vec.dtype != np.float64 or not vec.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous (K, n) float64 array")
+    else:
+        vec = None
     z = np.zeros(2 * K) if twist else None
     info = LanczosInfo()
     st = lib.hs_eigs_host(L, _dp(hh), float(sigma), K, m_max, tol, seed, int(mixed), PRECOND[precond],
-                          minres_tol, inner_tol, int(sm_budget), _dp(ev), _dp(vec), _dp(res), _dp(z),
-                          ctypes.byref(info))
+                          minres_tol, inner_tol, int(minres_kmax), int(sm_budget), _dp(ev), _dp(vec),
+                          _dp(res), _dp(z), ctypes.byref(info))
     if st not in (HS_OK, HS_NOT_CONVERGED):
         raise HSError(st, "hs_eigs_host")
     zz = (z[0::2] + 1j * z[1::2]) if twist else None

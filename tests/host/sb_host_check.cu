@@ -7,8 +7,10 @@
 // of anything not staged shows up in y. Usage:
 //   sb_host_check L k KS sigma shift dir
 // reads dir/h.bin (L doubles) and dir/x.bin (n doubles), writes dir/y64.bin
-// and dir/y32.bin (n doubles each; the FP32 result widened). shift offsets x
-// and y by that many elements from a 16-byte boundary.
+// and dir/y32.bin (n doubles each; the FP32 result widened), and the
+// preconditioner entries of the MINRES row passes: dir/mrow.bin (row norm),
+// dir/mjac.bin (Jacobi), dir/mrow32.bin (row norm in FP32, widened). shift
+// offsets x and y by that many elements from a 16-byte boundary.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -81,6 +83,42 @@ static void run(const HostPlan& P, const T* x, T* y, double sigma) {
   }
 }
 
+// The preconditioner entries of the MINRES row passes (k_sbrows): per row,
+// a_ii - sigma and the antiparallel-bond count from RowCtx / sb_diag, then
+// M_ii from sb_precond, in the kernel's order over pairs and sub-blocks.
+template <typename T, int PC>
+static void precond_rows(const HostPlan& P, T* out, double sigma) {
+  for (const int2 pr : P.pairs) {
+    for (int s = 0; s < 2; ++s) {
+      const int id = s ? pr.y : pr.x;
+      if (id < 0) continue;
+      const Sup& H = P.sup[id];
+      const uint32_t hm = H.meta;
+      const int wq = (int)(hm & 0xFF);
+      for (int i = 0; i < P.nvalid[wq]; ++i) {
+        const int m = P.order[(wq << P.km) + i];
+        const Sub& B = P.sub[(wq << P.km) + m];
+        const uint32_t bm = B.meta;
+        const int w = (int)(bm & 0xFF);
+        RowCtx<T> c;
+        c.low = P.low.data() + P.cls_off[w];
+        c.dlow = P.dlow.data() + P.cls_off[w];
+        c.mbit0 = (bm >> 16) & 1u;
+        c.ttop = (hm >> 17) & 1u;
+        const uint32_t anti_ks = ((bm >> 17) & 1u) ^ ((hm >> 16) & 1u);
+        c.nfix = (int)((bm >> 8) & 0xFF) + (int)anti_ks + (int)((hm >> 8) & 0xFF);
+        c.uni = (T)(B.dmid + H.dT - sigma + (anti_ks ? -0.25 : 0.25));
+        c.C = P.cls_C[w];
+        for (int r = 0; r < c.C; ++r) {
+          int naf;
+          const T am = sb_diag<T>(c, r, naf);
+          out[H.R + B.lo + r] = sb_precond<PC, T>(am, naf);
+        }
+      }
+    }
+  }
+}
+
 static bool read_all(const char* fn, void* p, size_t bytes) {
   FILE* f = fopen(fn, "rb");
   if (!f) return false;
@@ -136,6 +174,19 @@ int main(int argc, char** argv) {
   for (size_t i = 0; i < n; ++i) y32[i] = y4[i];
   snprintf(fn, sizeof fn, "%s/y32.bin", dir);
   if (!write_all(fn, y32.data(), sizeof(double) * n)) return 5;
+  // preconditioner entries (row norm and Jacobi, FP64 and FP32 widened)
+  std::vector<double> mr(n, NAN), mj(n, NAN), m32(n, NAN);
+  std::vector<float> mf(n, NAN);
+  precond_rows<double, 2>(P, mr.data(), sigma);
+  precond_rows<double, 1>(P, mj.data(), sigma);
+  precond_rows<float, 2>(P, mf.data(), sigma);
+  for (size_t i = 0; i < n; ++i) m32[i] = mf[i];
+  snprintf(fn, sizeof fn, "%s/mrow.bin", dir);
+  if (!write_all(fn, mr.data(), sizeof(double) * n)) return 5;
+  snprintf(fn, sizeof fn, "%s/mjac.bin", dir);
+  if (!write_all(fn, mj.data(), sizeof(double) * n)) return 5;
+  snprintf(fn, sizeof fn, "%s/mrow32.bin", dir);
+  if (!write_all(fn, m32.data(), sizeof(double) * n)) return 5;
   printf("ok n=%zu pairs=%zu\n", n, P.pairs.size());
   return 0;
 }

@@ -18,30 +18,81 @@ def _sys(L, h=3.0, seed=0, sigma=0.1234):
     return hv, H, diag, A, sigma
 
 
+def separated_sigma(diag):
+    """A shift in the widest gap between neighbouring diagonal values within
+    the middle half of their range: Jacobi's M = |a_ii - sigma| then stays away
+    from zero, and so does every preconditioner's spread."""
+    d = np.sort(diag)
+    gaps = d[1:] - d[:-1]
+    centres = 0.5 * (d[1:] + d[:-1])
+    mid, half = 0.5 * (d[0] + d[-1]), 0.25 * (d[-1] - d[0])
+    return float(centres[np.argmax(np.where(np.abs(centres - mid) < half, gaps, -1.0))])
+
+
+# Element-wise bounds on |x_gpu - x_oracle| / max|x_oracle| after k iterations
+# of Algorithm 2. Both sides run the same recurrence; they differ only in the
+# order of the reductions (dot products of n terms), which perturbs alpha_k
+# and beta_k by a few ulps, and in FP32 by the FP32 rounding of every vector
+# operation. Measured on GB300 with a well-separated shift: at most 5e-15
+# (k <= 7) and 3e-14 (k = 20) in FP64, 9e-7 and 1e-5 in FP32, whatever the
+# preconditioner; the bounds leave a factor 10-30.
+TOL64 = {1: 1e-13, 2: 1e-13, 3: 1e-13, 7: 1e-13, 20: 1e-12}
+TOL32 = {1: 1e-5, 2: 1e-5, 3: 1e-5, 7: 1e-5, 20: 1e-4}
+
+
 @pytest.mark.parametrize("L", [6, 8, 10, 12])
 @pytest.mark.parametrize("kind", ["id", "jacobi", "row"])
 @pytest.mark.parametrize("k", [1, 2, 3, 7, 20])
-def test_iterates_match_oracle_fp64(L, kind, k):
-    """x_k after k iterations of Algorithm 2 (FP64): same algorithm, so the
-    iterates agree up to the rounding of the reductions."""
+def test_iterates_match_oracle_elementwise(L, kind, k):
+    """x_k after k iterations of Algorithm 2, FP64 and FP32, element by
+    element against the oracle, at a shift where every preconditioner is
+    well conditioned (the ill-conditioned Jacobi case is the next test)."""
+    hs = need_gpu()
+    hv = inputs.disorder(L, 3.0, 0)
+    H, diag, st = hamiltonian.build(L, hv)
+    sigma = separated_sigma(diag)
+    A = (H - sigma * sp.identity(H.shape[0])).tocsr()
+    if k > A.shape[0] // 4:
+        pytest.skip("k near n: the Krylov space is exhausted and the recurrence runs on rounding")
+    b = inputs.gaussian(A.shape[0], 11)
+    M = hamiltonian.precond_diag(H, diag, sigma, kind)
+    assert M.max() / M.min() < 1e4
+    xr, kr, phir = minres.pminres(A, b, 1.0 / M, kmax=k, tol=0.0)
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        x, info = c.minres(to_dev(b), tol=0.0, kmax=k, precond=kind, allow_not_converged=True)
+        x32, i32 = c.minres_f32(to_dev(b, torch.float32), tol=0.0, kmax=k, precond=kind,
+                                allow_not_converged=True)
+    assert info["iters"] == k and i32["iters"] == k
+    scale = np.abs(xr).max()
+    assert np.abs(x.cpu().numpy() - xr).max() <= TOL64[k] * scale
+    assert np.abs(x32.cpu().double().numpy() - xr).max() <= TOL32[k] * scale
+    phi_ref = abs(phir) / np.sqrt(b @ (b / M))
+    assert abs(info["phi"] - phi_ref) <= TOL64[k] * max(phi_ref, 1e-300) * 10
+
+
+@pytest.mark.parametrize("L", [8, 12, 16])
+@pytest.mark.parametrize("kind", ["id", "jacobi", "row"])
+@pytest.mark.parametrize("k", [1, 3, 7, 20])
+def test_iterates_minimise_the_residual(L, kind, k):
+    """Eq. (minres_solution): x_k minimises ||b - A x||_{M^-1} over the Krylov
+    space, and the minimum is |phi_k|. At sigma = 0.1234 some a_ii lie close to
+    sigma, so Jacobi's M spans 1e5: the minimiser is then ill-conditioned (the
+    iterates of two correct implementations differ by up to 1e-9 relative in
+    FP64), but the minimum is not. The oracle's explicit A gives the true
+    M^-1-norm residual of the GPU iterate, which must equal the oracle's
+    |phi_k|; a wrong row or a wrong preconditioner entry would raise it."""
     hs = need_gpu()
     hv, H, diag, A, sigma = _sys(L)
     if k > A.shape[0] // 4:
-        pytest.skip("k near n: the Krylov space is exhausted and the recurrence runs on rounding")
+        pytest.skip("k near n")
     b = inputs.gaussian(A.shape[0], 11)
     M = hamiltonian.precond_diag(H, diag, sigma, kind)
     xr, kr, phir = minres.pminres(A, b, 1.0 / M, kmax=k, tol=0.0)
     with hs.Chain(L, hv, sigma=sigma) as c:
         x, info = c.minres(to_dev(b), tol=0.0, kmax=k, precond=kind, allow_not_converged=True)
-    assert info["iters"] == k
-    x = x.cpu().numpy()
-    # the reductions round in a different order; the recurrence amplifies
-    # that by the spread of the preconditioner and, as the Lanczos vectors
-    # lose orthogonality, with k (k reaches n = 20 at L = 6)
-    spread = M.max() / M.min()
-    tol = (1e-12 if k <= 7 else 1e-8) * spread
-    assert np.linalg.norm(x - xr) <= tol * np.linalg.norm(xr)
-    assert abs(info["phi"] - abs(phir) / np.sqrt(b @ (b / M))) <= tol
+    r = b - A @ x.cpu().numpy()
+    got = np.sqrt(r @ (r / M))
+    assert abs(got - abs(phir)) <= 1e-10 * abs(phir), (got, abs(phir))
 
 
 @pytest.mark.parametrize("L", [8, 12, 14])
@@ -62,15 +113,21 @@ def test_solve_fp64(L, kind):
 
 @pytest.mark.parametrize("L", [10, 14])
 def test_fp32_solver(L):
+    """A whole FP32 solve to 1e-4: its true residual (oracle A, FP64) reaches
+    the tolerance up to the FP32 rounding of A x (~ n_bonds 2^-24 |A| |x|)."""
     hs = need_gpu()
     hv, H, diag, A, sigma = _sys(L, seed=2)
     b = inputs.gaussian(A.shape[0], 4).astype(np.float32)
+    M = hamiltonian.precond_diag(H, diag, sigma, "row")
     with hs.Chain(L, hv, sigma=sigma) as c:
         x, info = c.minres_f32(to_dev(b), tol=1e-4, precond="row", allow_not_converged=True)
     x = x.cpu().double().numpy()
-    rel = np.linalg.norm(A @ x - b) / np.linalg.norm(b)
-    assert rel < 1e-2, rel
-    assert info["iters"] > 0
+    bb = b.astype(np.float64)
+    r = bb - A @ x
+    rel = np.sqrt(r @ (r / M)) / np.sqrt(bb @ (bb / M))
+    floor = (L + 4) * 2.0 ** -24 * np.linalg.norm(abs(A) @ np.abs(x)) / np.linalg.norm(bb)
+    assert info["status"] == 0 and 0 < info["iters"]
+    assert rel <= 1e-4 * 1.01 + 30 * floor, (rel, floor)
 
 
 @pytest.mark.parametrize("L", [10, 14, 16])

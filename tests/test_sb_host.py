@@ -68,6 +68,18 @@ def test_superblock_rows_vs_explicit_matrix(checker, tmp_path, L, k, KS):
         assert np.isfinite(y64).all() and np.isfinite(y32).all()
         assert np.abs(y64 - ref).max() <= 1e-14 * scale
         assert (np.abs(y32 - ref32) <= bound32 + 1e-30).all()
+    # preconditioner entries of the MINRES row passes (Sec. II, Eq. (rownorm)
+    # and M_Jacobi) against the oracle's, row by row
+    mrow = np.fromfile(tmp_path / "mrow.bin")
+    mjac = np.fromfile(tmp_path / "mjac.bin")
+    mrow32 = np.fromfile(tmp_path / "mrow32.bin")
+    ref_row = hamiltonian.precond_diag(H, diag, sigma, "row")
+    ref_jac = np.abs(diag - sigma)
+    assert np.abs(mrow - ref_row).max() <= 1e-14 * ref_row.max()
+    assert np.abs(mjac - ref_jac).max() <= 1e-14 * (np.abs(diag).max() + 1)
+    # FP32: a_ii - sigma from FP32 terms of magnitude up to |a_ii| + L, then
+    # one square root
+    assert (np.abs(mrow32 - ref_row) <= 2.0 ** -22 * (np.abs(diag) + L + 1)).all()
 
 
 def test_plan_rejects_splits_out_of_range(checker, tmp_path):
