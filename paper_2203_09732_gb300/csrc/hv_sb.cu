@@ -75,6 +75,7 @@ static hs_status make_dev(hs_handle* hd, int KS, DevPlan** out) {
     g.cls_C[i] = P.cls_C[i];
   }
   for (int i = 0; i <= WQ_MAX; ++i) g.nvalid[i] = P.nvalid[i];
+  g.dscale = P.dscale;
   d->smem = smem_bytes<T>((int)P.low.size(), P.km);
   auto kern = kernel_of<T>();
   int nb = 0;

@@ -96,6 +96,7 @@ struct Geo {
   int cls_off[K_MAX + 2];
   int cls_C[K_MAX + 2];
   int nvalid[WQ_MAX + 1];      // valid m per class
+  double dscale;               // L/4 + sum_j |h_j| / 2: bound of |a_ii|
 };
 
 // Host tables of one plan.
@@ -110,6 +111,7 @@ struct HostPlan {
   int cls_off[K_MAX + 2] = {0};
   int cls_C[K_MAX + 2] = {0};
   int nvalid[WQ_MAX + 1] = {0};
+  double dscale = 0.0;
 };
 
 inline uint64_t binom64(int n, int r) {
@@ -149,6 +151,8 @@ inline bool build_plan(int L, const double* h, int k, int KS, HostPlan* P) {
   P->km = km;
   P->KS = KS;
   P->tb = tb;
+  P->dscale = 0.25 * L;
+  for (int j = 0; j < L; ++j) P->dscale += 0.5 * (h[j] < 0 ? -h[j] : h[j]);
   // low patterns
   int off = 0;
   for (int w = 0; w <= k; ++w) {

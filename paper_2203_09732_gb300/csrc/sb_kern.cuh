@@ -226,6 +226,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : 2) k_sbrows(Geo g, co
   const T* dA = (const T*)(odd ? v.d1 : v.d0);   // d_{k-2}
   T* dB = (T*)(odd ? v.d0 : v.d1);               // d_{k-3} -> d_{k-1}
   T* xv = (T*)v.x;
+  // rounding bound of a_ii - sigma as assembled from the tables (a few
+  // additions of terms up to dscale + |sigma|)
+  const T mtiny = (T)(8.0 * (sizeof(T) == 8 ? 2.220446049250313e-16 : 1.1920928955078125e-7) *
+                      (g.dscale + fabs(sigma)));
   T acc = T(0), zm = T(0);
   for (int pi = blockIdx.x; pi < g.npairs; pi += gridDim.x) {
     const int2 pr = g.pairs[pi];
@@ -259,35 +263,61 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 8 ? 1 : 2) k_sbrows(Geo g, co
       c.uni = (T)(__ldg(&B->dmid) + H.dT - sigma + (anti_ks ? -0.25 : 0.25));
       c.C = g.cls_C[w];
       const uint32_t base = H.R + __ldg(&B->lo);
-      for (int r = lane; r < c.C; r += 32) {
-        int naf;
-        const T am = sb_diag<T>(c, r, naf);
-        const T mm = sb_precond<PC, T>(am, naf);
-        const uint32_t i = base + (uint32_t)r;
-        if constexpr (MODE == ROWS_INIT) {
-          const T b = bv[i];
-          zm += mm == T(0) ? T(1) : T(0);
-          const T q = mm == T(0) ? T(0) : b / mm;
-          ((T*)v.q1)[i] = q;
-          ((T*)v.q0)[i] = T(0);
-          ((T*)v.d0)[i] = T(0);
-          ((T*)v.d1)[i] = T(0);
-          ((T*)v.x)[i] = T(0);
-          acc += q * b;
-        } else {
-          const T qold = qn[i];                              // q_{k-1}
-          if (doC) {
-            // d_{k-1} = (q_{k-1} / beta_{k-1} - delta d_{k-2} - eps d_{k-3}) / gamma_{k-1};
-            // x_{k-1} = x_{k-2} + tau_{k-1} d_{k-1}
-            const T d = cq * qold + cd1 * dA[i] + cd2 * dB[i];
-            dB[i] = d;
-            xv[i] += tau * d;
+      // RB rows per lane at a time: every load of the batch is issued before
+      // any arithmetic or store, so that 6 RB loads per lane are in flight
+      constexpr int RB = 4;
+      for (int r0 = lane; r0 < c.C; r0 += 32 * RB) {
+        T va[RB], vb[RB], vc[RB], vd[RB], ve[RB], vf[RB];
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+          const int r = r0 + 32 * j;
+          const uint32_t i = base + (uint32_t)(r < c.C ? r : 0);
+          const bool ok = r < c.C;
+          if constexpr (MODE == ROWS_INIT) {
+            va[j] = ok ? bv[i] : T(0);
+          } else {
+            va[j] = ok ? qn[i] : T(0);                                // q_{k-1}
+            vb[j] = ok && doC ? dA[i] : T(0);                         // d_{k-2}
+            vc[j] = ok && doC ? dB[i] : T(0);                         // d_{k-3}
+            vd[j] = ok && doC ? xv[i] : T(0);                         // x
+            ve[j] = ok && doQ ? pv[i] : T(0);                         // p
+            vf[j] = ok && doQ ? qc[i] : T(0);                         // q_k
           }
-          if (doQ) {
-            // q_{k+1} = M^-1 p / beta_k - (alpha_k / beta_k) q_k - (beta_k / beta_{k-1}) q_{k-1}
-            const T q = (pv[i] / mm) * c1 - c2 * qc[i] - c3 * qold;
-            qn[i] = q;
-            acc += mm * q * q;                               // beta_{k+1}^2 = q . M q
+        }
+#pragma unroll
+        for (int j = 0; j < RB; ++j) {
+          const int r = r0 + 32 * j;
+          if (r >= c.C) continue;
+          int naf;
+          const T am = sb_diag<T>(c, r, naf);
+          const T mm = sb_precond<PC, T>(am, naf);
+          const uint32_t i = base + (uint32_t)r;
+          if constexpr (MODE == ROWS_INIT) {
+            // a Jacobi entry at the rounding level of a_ii - sigma counts as
+            // a_ii = sigma (Sec. II assumes a_ii != sigma)
+            const bool zero = !(mm > mtiny);
+            zm += zero ? T(1) : T(0);
+            const T q = zero ? T(0) : va[j] / mm;
+            ((T*)v.q1)[i] = q;
+            ((T*)v.q0)[i] = T(0);
+            ((T*)v.d0)[i] = T(0);
+            ((T*)v.d1)[i] = T(0);
+            ((T*)v.x)[i] = T(0);
+            acc += q * va[j];
+          } else {
+            if (doC) {
+              // d_{k-1} = (q_{k-1} / beta_{k-1} - delta d_{k-2} - eps d_{k-3}) / gamma_{k-1};
+              // x_{k-1} = x_{k-2} + tau_{k-1} d_{k-1}
+              const T d = cq * va[j] + cd1 * vb[j] + cd2 * vc[j];
+              dB[i] = d;
+              xv[i] = vd[j] + tau * d;
+            }
+            if (doQ) {
+              // q_{k+1} = M^-1 p / beta_k - (alpha_k / beta_k) q_k - (beta_k / beta_{k-1}) q_{k-1}
+              const T q = (ve[j] / mm) * c1 - c2 * vf[j] - c3 * va[j];
+              qn[i] = q;
+              acc += mm * q * q;                             // beta_{k+1}^2 = q . M q
+            }
           }
         }
       }
