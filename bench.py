@@ -221,7 +221,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("common.cuh", "sb.cuh", "sb_kern.cuh", "hv_sb.cu"):
+    for f in ("common.cuh", "sb.cuh", "sb_kern.cuh", "sb4.cuh", "sb4_kern.cuh", "hv_sb.cu"):
         h.update(open(os.path.join(ROOT, "paper_2203_09732_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -250,7 +250,11 @@ def profiled_traffic(name):
 def hv_kernel_name(L):
     e = os.environ.get("HS_HV_SB")
     on = (e == "1" and L >= 22) if e is not None else L >= 24
-    return "k_sbhv<float, MODE_HV> (superblock form)" if on else "k_matvec<float> (block form)"
+    if not on:
+        return "k_matvec<float> (block form)"
+    if os.environ.get("HS_SB4") == "0":
+        return "k_sbhv<float, MODE_HV> (ten-low-bit superblock form)"
+    return "k_sb4<float, MODE_HV> (four-low-bit superblock form, one lane per sub-block)"
 
 
 def hv_roofline(torch, hs, L, stream):

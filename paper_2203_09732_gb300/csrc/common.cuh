@@ -147,6 +147,8 @@ struct hs_handle {
 
   // superblock H x plans (hv_sb.cu): [0] FP32, [1] FP64; null where not built
   void* sb_plan[2] = {nullptr, nullptr};
+  // four-low-bit superblock plans (sb4.cuh): [0] FP32, [1] FP64
+  void* sb4_plan[2] = {nullptr, nullptr};
   // superblock MINRES chunk graphs (minres_sb.cu), [precision][preconditioner],
   // with the grids (pass A, pass B) and the workspace they were captured for
   cudaGraphExec_t sbgraph[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};

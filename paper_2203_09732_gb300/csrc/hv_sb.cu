@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "sb.cuh"
+#include "sb4_kern.cuh"
 #include "sb_kern.cuh"
 
 namespace hs {
@@ -94,6 +95,94 @@ static hs_status make_dev(hs_handle* hd, int KS, DevPlan** out) {
 
 }  // namespace sb
 
+namespace sb4 {
+
+constexpr int NT4_F = 512;   // FP32: two CTAs of 512 threads per SM
+constexpr int NT4_D = 256;   // FP64: more registers per thread
+
+template <typename T>
+auto kernel4() {
+  if constexpr (sizeof(T) == 8) return k_sb4<double, NT4_D, 2, 4, sb::MODE_HV>;
+  else return k_sb4<float, NT4_F, 2, 4, sb::MODE_HV>;
+}
+
+template <typename T>
+static hs_status make_dev4(hs_handle* hd, int KS, DevPlan4** out) {
+  *out = nullptr;
+  HostPlan4 P;
+  if (!build_plan4(hd->L, hd->h, KS, &P)) return HS_OK;
+  const sb::HostPlan& B = P.base;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  struct Part { const void* src; size_t bytes; size_t at; };
+  std::vector<Part> parts = {
+      {B.sup.data(), B.sup.size() * sizeof(sb::Sup), 0},
+      {B.pairs.data(), B.pairs.size() * sizeof(int2), 0},
+      {P.slotmap.data(), P.slotmap.size() * sizeof(uint16_t), 0},
+      {P.order.data(), P.order.size() * sizeof(uint16_t), 0},
+      {P.lo.data(), P.lo.size() * sizeof(uint16_t), 0},
+      {P.dmid_f.data(), P.dmid_f.size() * sizeof(float), 0},
+      {P.dmid_d.data(), P.dmid_d.size() * sizeof(double), 0},
+      {P.dl_f.data(), P.dl_f.size() * sizeof(float), 0},
+      {P.dl_d.data(), P.dl_d.size() * sizeof(double), 0}};
+  size_t total = 0;
+  for (Part& q : parts) {
+    q.at = total;
+    total += al(q.bytes);
+  }
+  std::vector<char> host(total, 0);
+  for (const Part& q : parts) std::memcpy(host.data() + q.at, q.src, q.bytes);
+  DevPlan4* d = new DevPlan4();
+  if (dev_alloc(hd, &d->mem, total) != HS_OK) {
+    delete d;
+    return fail(hd, HS_OOM, "superblock table allocation failed");
+  }
+  // pageable source: the copy is staged before the call returns
+  if (cudaMemcpyAsync(d->mem, host.data(), total, cudaMemcpyHostToDevice, hd->stream) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(hd, d->mem);
+    delete d;
+    return fail(hd, HS_CUDA, "superblock table upload failed");
+  }
+  char* base = static_cast<char*>(d->mem);
+  Geo4& g = d->geo;
+  g.sup = reinterpret_cast<const sb::Sup*>(base + parts[0].at);
+  g.pairs = reinterpret_cast<const int2*>(base + parts[1].at);
+  g.slotmap = reinterpret_cast<const uint16_t*>(base + parts[2].at);
+  g.order = reinterpret_cast<const uint16_t*>(base + parts[3].at);
+  g.lo = reinterpret_cast<const uint16_t*>(base + parts[4].at);
+  g.dmid_f = reinterpret_cast<const float*>(base + parts[5].at);
+  g.dmid_d = reinterpret_cast<const double*>(base + parts[6].at);
+  g.dl_f = reinterpret_cast<const float*>(base + parts[7].at);
+  g.dl_d = reinterpret_cast<const double*>(base + parts[8].at);
+  g.npairs = (int)B.pairs.size();
+  g.km = B.km;
+  g.KS = B.KS;
+  g.cmax = P.cmax;
+  for (int i = 0; i <= WQ_MAX; ++i) {
+    g.slot_off[i] = P.slot_off[i];
+    g.order_off[i] = P.order_off[i];
+    g.nvalid[i] = P.nvalid[i];
+  }
+  g.dscale = B.dscale;
+  d->smem = smem_bytes4<T>(g.km, g.cmax);
+  auto kern = kernel4<T>();
+  const int nt = sizeof(T) == 8 ? NT4_D : NT4_F;
+  int nb = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) ==
+          cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nt, d->smem) == cudaSuccess &&
+      nb > 0) {
+    d->grid = std::min(g.npairs, nb * hd->num_sms);
+    d->ok = 1;
+  } else {
+    cudaGetLastError();
+  }
+  *out = d;
+  return HS_OK;
+}
+
+}  // namespace sb4
+
 // Superblock windows of k + 4 bits (16 slots of 256 rows per superblock: x
 // slots and sums of a pair take 65 KB in FP32, two CTAs per SM) and at most
 // L - 10 bits, so that a chain has at least 512 superblock pairs to spread
@@ -109,6 +198,17 @@ hs_status sb_setup(hs_handle* hd) {
   st = sb::make_dev<double>(hd, ks64, &d);
   if (st != HS_OK) return st;
   hd->sb_plan[1] = d;
+  // four-low-bit plans (sb4.cuh): 14-bit windows in FP32, 13 in FP64 (the
+  // slots and sums of a pair take about 96 KB either way); HS_SB4_KS32 and
+  // HS_SB4_KS64 override them (tests of small chains)
+  int k32 = std::min(14, hd->L - 6), k64 = std::min(13, hd->L - 6);
+  if (const char* e = getenv("HS_SB4_KS32")) k32 = atoi(e);
+  if (const char* e = getenv("HS_SB4_KS64")) k64 = atoi(e);
+  sb4::DevPlan4* d4 = nullptr;
+  if ((st = sb4::make_dev4<float>(hd, k32, &d4)) != HS_OK) return st;
+  hd->sb4_plan[0] = d4;
+  if ((st = sb4::make_dev4<double>(hd, k64, &d4)) != HS_OK) return st;
+  hd->sb4_plan[1] = d4;
   return HS_OK;
 }
 
@@ -120,12 +220,44 @@ void sb_release(hs_handle* hd) {
       delete d;
     }
     hd->sb_plan[i] = nullptr;
+    auto* d4 = static_cast<sb4::DevPlan4*>(hd->sb4_plan[i]);
+    if (d4) {
+      dev_free(hd, d4->mem);
+      delete d4;
+    }
+    hd->sb4_plan[i] = nullptr;
   }
+}
+
+// HS_SB4=0 turns the four-low-bit form off (tests compare forms); it is used
+// wherever its plan applies.
+static bool want_sb4() {
+  const char* e = getenv("HS_SB4");
+  return !(e && e[0] == '0');
 }
 
 hs_status launch_matvec_sb(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted,
                            bool* used) {
   *used = false;
+  {
+    auto* d4 = static_cast<sb4::DevPlan4*>(hd->sb4_plan[dt == HS_F32 ? 0 : 1]);
+    const size_t es = dt == HS_F32 ? sizeof(float) : sizeof(double);
+    if (want_sb4() && d4 && d4->ok && ((uintptr_t)x % es) == 0 && ((uintptr_t)y % es) == 0) {
+      const sb::MinresArgs none{};
+      if (dt == HS_F32)
+        sb4::kernel4<float>()<<<d4->grid, sb4::NT4_F, d4->smem, hd->stream>>>(
+            d4->geo, static_cast<const float*>(x), static_cast<float*>(y), hd->d_sigma, shifted,
+            none);
+      else
+        sb4::kernel4<double>()<<<d4->grid, sb4::NT4_D, d4->smem, hd->stream>>>(
+            d4->geo, static_cast<const double*>(x), static_cast<double*>(y), hd->d_sigma, shifted,
+            none);
+      count_launches(1);
+      HS_CUDA_TRY(hd, cudaGetLastError());
+      *used = true;
+      return HS_OK;
+    }
+  }
   auto* d = static_cast<sb::DevPlan*>(hd->sb_plan[dt == HS_F32 ? 0 : 1]);
   if (!d || !d->ok) return HS_OK;
   const size_t es = dt == HS_F32 ? sizeof(float) : sizeof(double);

@@ -13,6 +13,7 @@
 
 #include "common.cuh"
 #include "minres_scalar.cuh"
+#include "sb4_kern.cuh"
 #include "sb_kern.cuh"
 
 namespace hs {
@@ -25,6 +26,18 @@ constexpr int SB_CHUNK = 8; // iterations per graph replay
 
 template <typename T>
 auto kern_A() { return sb::k_sbhv<T, NT_A, 2, 4, sb::MODE_MINRES>; }
+// pass A on the four-low-bit layout (sb4.cuh), where its plan applies
+constexpr int NT_A4F = 512, NT_A4D = 256;
+template <typename T>
+constexpr int nt_a4() { return sizeof(T) == 8 ? NT_A4D : NT_A4F; }
+template <typename T>
+auto kern_A4() { return sb4::k_sb4<T, nt_a4<T>(), 2, 4, sb::MODE_MINRES>; }
+
+// HS_SB4=0 keeps pass A on the ten-low-bit layout (tests compare forms).
+bool want_sb4() {
+  const char* e = getenv("HS_SB4");
+  return !(e && e[0] == '0');
+}
 template <typename T, int PC, int MODE>
 auto kern_R() { return sb::k_sbrows<T, PC, MODE, NT_R>; }
 
@@ -52,9 +65,12 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
   auto* d = static_cast<sb::DevPlan*>(hd->sb_plan[ti]);
   if (!d || !d->ok) return HS_OK;
   const sb::Geo& g = d->geo;
-  const size_t smA = d->smem;
+  auto* d4 = static_cast<sb4::DevPlan4*>(hd->sb4_plan[ti]);
+  const bool use4 = want_sb4() && d4 && d4->ok;
+  const size_t smA = use4 ? d4->smem : d->smem;
   const size_t smR = sb::rows_smem_bytes<T>(1 << g.k);
-  const int gA = grid_of(hd, kern_A<T>(), NT_A, smA, g.npairs);
+  const int gA = use4 ? grid_of(hd, kern_A4<T>(), nt_a4<T>(), smA, d4->geo.npairs)
+                      : grid_of(hd, kern_A<T>(), NT_A, smA, g.npairs);
   const int gI = grid_of(hd, kern_R<T, PC, sb::ROWS_INIT>(), NT_R, smR, g.npairs);
   const int gB = grid_of(hd, kern_R<T, PC, sb::ROWS_B>(), NT_R, smR, g.npairs);
   if (gA < 1 || gI < 1 || gB < 1) return HS_OK;
@@ -72,7 +88,8 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
   // and this workspace
   cudaGraphExec_t& exec = hd->sbgraph[ti][PC];
   int* key = hd->sbgraph_key[ti][PC];
-  if (exec && (key[0] != gA || key[1] != gB || hd->sbgraph_ws[ti] != v.q0)) {
+  const int keyA = gA | (use4 ? 1 << 30 : 0);
+  if (exec && (key[0] != keyA || key[1] != gB || hd->sbgraph_ws[ti] != v.q0)) {
     cudaGraphExecDestroy(exec);
     exec = nullptr;
   }
@@ -86,7 +103,10 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
       mA.counter = hd->d_counter + 1;
       mB.counter = hd->d_counter + 2;
       for (int it = 0; it < SB_CHUNK; ++it) {
-        kern_A<T>()<<<gA, NT_A, smA, cs>>>(g, nullptr, nullptr, hd->d_sigma, 1, mA);
+        if (use4)
+          kern_A4<T>()<<<gA, nt_a4<T>(), smA, cs>>>(d4->geo, nullptr, nullptr, hd->d_sigma, 1, mA);
+        else
+          kern_A<T>()<<<gA, NT_A, smA, cs>>>(g, nullptr, nullptr, hd->d_sigma, 1, mA);
         kern_R<T, PC, sb::ROWS_B>()<<<gB, NT_R, smR, cs>>>(g, nullptr, mB, 0.0, 0, hd->d_sigma);
       }
       e = cudaStreamEndCapture(cs, &graph);
@@ -100,7 +120,7 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
       exec = nullptr;
       return fail(hd, HS_CUDA, std::string("superblock MINRES graph: ") + cudaGetErrorString(e));
     }
-    key[0] = gA;
+    key[0] = keyA;
     key[1] = gB;
     hd->sbgraph_ws[ti] = v.q0;
   }

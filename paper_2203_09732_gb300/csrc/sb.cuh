@@ -141,11 +141,14 @@ inline int popc_host(uint32_t v) {
 
 // Build the plan for chain length L with fields h[0..L-1], k low bits and a
 // KS-bit window. Returns false (and leaves the plan empty) if the split does
-// not apply: needs 2 <= k <= K_MAX, 1 <= KS - k <= KM_MAX, 2 <= L - KS <= HH_MAX + 1.
-inline bool build_plan(int L, const double* h, int k, int KS, HostPlan* P) {
+// not apply: needs 2 <= k <= K_MAX, 1 <= KS - k <= km_max, 2 <= L - KS <= HH_MAX + 1.
+// The per-sub-block mid offsets (Sub::md, read by the product of this file)
+// are filled only for km <= KM_MAX; a larger km_max serves sb4.cuh, which
+// finds mid neighbours by bit arithmetic instead.
+inline bool build_plan(int L, const double* h, int k, int KS, HostPlan* P, int km_max = KM_MAX) {
   *P = HostPlan{};
   const int N = L / 2, km = KS - k, tb = L - KS;
-  if (k < 2 || k > K_MAX || km < 1 || km > KM_MAX || tb < 2 || tb - 1 > HH_MAX || KS > WQ_MAX)
+  if (k < 2 || k > K_MAX || km < 1 || km > km_max || tb < 2 || tb - 1 > HH_MAX || KS > WQ_MAX)
     return false;
   P->k = k;
   P->km = km;
@@ -224,7 +227,8 @@ inline bool build_plan(int L, const double* h, int k, int KS, HostPlan* P) {
           d += 0.25;
         } else {
           d -= 0.25;
-          b.md[nmd++] = ((m ^ (3 << j)) - m) * SL;
+          if (km <= KM_MAX) b.md[nmd] = ((m ^ (3 << j)) - m) * SL;
+          ++nmd;
         }
       }
       for (int j = 0; j < km; ++j) d -= h[k + j] * (((m >> j) & 1) ? 0.5 : -0.5);

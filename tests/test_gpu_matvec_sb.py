@@ -1,7 +1,9 @@
-"""GPU parity of the superblock form of H x (row a3 for long chains): the
+"""GPU parity of the superblock forms of H x (row a3 for long chains): the
 matrix-free (H - sigma) x of Eq. (1) with the x tiles of two superblocks
 staged in shared memory, against the oracle's explicit sparse H and against
-the block form."""
+the block form. Two superblock forms: four low bits with one lane per
+sub-block (sb4, the default; HS_SB4=1) and ten low bits with one warp per
+sub-block (HS_SB4=0)."""
 import numpy as np
 import pytest
 
@@ -12,14 +14,16 @@ from tests.gpu_util import need_gpu, to_dev, torch
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("form", ["1", "0"])
 @pytest.mark.parametrize("L", [22, 24])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("shifted", [0, 1])
-def test_superblock_matvec_vs_oracle(L, dtype, shifted, monkeypatch):
-    """Every row against the explicit matrix (L = 22: 512 pairs of 12-bit
-    superblocks; L = 24: 14-bit superblocks in FP32, 13-bit in FP64)."""
+def test_superblock_matvec_vs_oracle(L, dtype, shifted, form, monkeypatch):
+    """Every row against the explicit matrix (sb4: 14-bit windows in FP32,
+    13-bit in FP64; ten-bit form: 12-bit windows at L = 22, 14/13-bit at 24)."""
     hs = need_gpu()
     monkeypatch.setenv("HS_HV_SB", "1")
+    monkeypatch.setenv("HS_SB4", form)
     h = inputs.disorder(L, 3.0, 300 + L)
     H, diag, st = hamiltonian.build(L, h)
     sigma = 0.41
@@ -40,12 +44,14 @@ def test_superblock_matvec_vs_oracle(L, dtype, shifted, monkeypatch):
         assert (np.abs(y - ref) <= bound + 1e-30).all()
 
 
+@pytest.mark.parametrize("form", ["1", "0"])
 @pytest.mark.parametrize("L", [24, 26, 28])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
-def test_superblock_matches_block_form(L, dtype, monkeypatch):
+def test_superblock_matches_block_form(L, dtype, form, monkeypatch):
     """Full-size launches: superblock form against the block (gather) form on
     the same x; the two differ only in the order of the row sums."""
     hs = need_gpu()
+    monkeypatch.setenv("HS_SB4", form)
     h = inputs.disorder(L, 3.7, 4)
     tdt = torch.float64 if dtype == "f64" else torch.float32
     with hs.Chain(L, h, sigma=0.1) as c:
@@ -61,15 +67,17 @@ def test_superblock_matches_block_form(L, dtype, monkeypatch):
     assert float((y1 - y0).abs().max()) <= tol
 
 
+@pytest.mark.parametrize("form", ["1", "0"])
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("offset", [1, 3])
-def test_superblock_unaligned_vectors(dtype, offset, monkeypatch):
+def test_superblock_unaligned_vectors(dtype, offset, form, monkeypatch):
     """x and y that start off a 16-byte boundary (views at an element offset):
     the staged copies and the stores follow the vectors, and the result is
     the same as with aligned vectors, element for element, with nothing
     written outside y."""
     hs = need_gpu()
     monkeypatch.setenv("HS_HV_SB", "1")
+    monkeypatch.setenv("HS_SB4", form)
     L = 24
     h = inputs.disorder(L, 3.0, 8)
     tdt = torch.float64 if dtype == "f64" else torch.float32
@@ -83,6 +91,32 @@ def test_superblock_unaligned_vectors(dtype, offset, monkeypatch):
         torch.cuda.synchronize()
     assert torch.equal(yb[offset:offset + c.n], y)
     assert bool(torch.isnan(yb[:offset]).all()) and bool(torch.isnan(yb[offset + c.n:]).all())
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_four_bit_form_sampled_rows_l28(dtype, monkeypatch):
+    """L = 28 (40,116,600 rows), the size of the benchmark, through the
+    default FP32 path (sb4) and sb4 in FP64: 300 sampled rows computed one by
+    one from Eq. (1)."""
+    hs = need_gpu()
+    monkeypatch.setenv("HS_HV_SB", "1")
+    L = 28
+    h = inputs.disorder(L, 3.7, 0)
+    n = inputs.dim(L)
+    rng = np.random.default_rng(28)
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    x = torch.randn(n, generator=torch.Generator().manual_seed(3), dtype=torch.float64).to(tdt)
+    sigma = 0.07
+    with hs.Chain(L, h, sigma=sigma) as c:
+        y = c.matvec(x.cuda(), shifted=True).cpu().double().numpy()
+    xs = x.double().numpy()
+    for i in np.concatenate([rng.integers(0, n, 300), [0, n - 1]]):
+        s = basis.unrank_count(int(i), L)
+        d, off = hamiltonian.row(L, h, s, sigma)
+        ref = d * xs[i] + sum(v * xs[j] for j, v in off)
+        mag = abs(d * xs[i]) + sum(abs(v * xs[j]) for j, v in off)
+        tol = 1e-14 * mag if dtype == "f64" else (L + 4) * 2.0 ** -23 * mag
+        assert abs(y[i] - ref) <= tol + 1e-300, (i, y[i], ref)
 
 
 def test_superblock_sampled_rows_l26(monkeypatch):

@@ -1,5 +1,6 @@
 """GPU parity of the superblock MINRES form (Algorithm 2 on the superblock
-layout: pass A = the superblock H x with the alpha dot, pass B = q_{k+1},
+layout: pass A = the superblock H x with the alpha dot (four-low-bit form by
+default, ten-bit form with HS_SB4=0), pass B = q_{k+1},
 beta_{k+1}, the Givens rotation and the d/x update of the previous iteration).
 It is the default from L = 24 on; HS_MINRES_SB=1 makes it the first choice
 wherever a superblock plan exists, and HS_SB_PLANS=1 with HS_KLO=4 builds
@@ -36,15 +37,17 @@ def l22():
     return L, hv, H, diag
 
 
+@pytest.mark.parametrize("form", ["1", "0"])
 @pytest.mark.parametrize("kind", ["id", "row"])
 @pytest.mark.parametrize("k", [1, 3, 7, 20])
-def test_iterates_match_oracle_l22(l22, kind, k, monkeypatch):
+def test_iterates_match_oracle_l22(l22, kind, k, form, monkeypatch):
     """FP64 and FP32 iterates of the superblock form at L = 22 (its k = 10
     tables, windows as at L = 28) element by element against the oracle.
     (At L = 22 the 705k diagonal values are so dense that some a_ii - sigma
     cancels at any shift, so Jacobi is checked by the next test.)"""
     hs = need_gpu()
     monkeypatch.setenv("HS_MINRES_SB", "1")
+    monkeypatch.setenv("HS_SB4", form)
     L, hv, H, diag = l22
     sigma = separated_sigma(diag)
     A = (H - sigma * sp.identity(H.shape[0])).tocsr()

@@ -92,3 +92,59 @@ def test_plan_rejects_splits_out_of_range(checker, tmp_path):
         r = subprocess.run([checker, str(L), str(k), str(KS), "0.0", "0", str(tmp_path)],
                            capture_output=True, text=True)
         assert r.returncode == 4 and "does not apply" in r.stdout
+
+
+@pytest.fixture(scope="module")
+def checker4(tmp_path_factory):
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not found")
+    out = tmp_path_factory.mktemp("sb4host") / "sb4_host_check"
+    src = os.path.join(HERE, "host", "sb4_host_check.cu")
+    r = subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-O2", "-o", str(out), src],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return str(out)
+
+
+# (L, KS) with k = 4 low bits: KS - 4 mid bits, L - KS top bits; the library's
+# window at L >= 22 is KS = 14 (FP32) and 13 (FP64)
+SPLITS4 = [(12, 5), (12, 8), (14, 6), (14, 10), (16, 8), (16, 12), (18, 13), (18, 14), (20, 14),
+           (22, 13), (22, 14), (24, 14)]
+
+
+@pytest.mark.parametrize("L,KS", SPLITS4)
+def test_four_bit_superblock_rows_vs_explicit_matrix(checker4, tmp_path, L, KS):
+    """The lane-per-sub-block row code: every row against the oracle's explicit
+    H in FP64 (1e-14) and FP32 (the rounding bound of an FP32 row sum), with NaN
+    in every slot element, G entry and guard element that the kernel must not
+    read."""
+    h = np.asarray(inputs.disorder(L, 3.0, 5 * L + KS), dtype=np.float64)
+    H, diag, st = hamiltonian.build(L, h)
+    x = inputs.gaussian(len(st), 3 + L)
+    h.tofile(tmp_path / "h.bin")
+    x.tofile(tmp_path / "x.bin")
+    sigma = -0.29
+    ref = H @ x - sigma * x
+    x32 = x.astype(np.float32).astype(np.float64)
+    ref32 = H @ x32 - sigma * x32
+    bound32 = (L + 4) * 2.0 ** -24 * (np.abs(diag - sigma) * np.abs(x32) + abs(H) @ np.abs(x32)) * 2
+    scale = np.abs(diag * x).max() + np.abs(x).max() * L
+    r = subprocess.run([checker4, str(L), str(KS), repr(sigma), str(tmp_path)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, (r.stdout, r.stderr)
+    y64 = np.fromfile(tmp_path / "y64.bin")
+    y32 = np.fromfile(tmp_path / "y32.bin")
+    assert np.isfinite(y64).all() and np.isfinite(y32).all()
+    assert np.abs(y64 - ref).max() <= 1e-14 * scale
+    assert (np.abs(y32 - ref32) <= bound32 + 1e-30).all()
+
+
+def test_four_bit_plan_rejects_splits_out_of_range(checker4, tmp_path):
+    """More than 10 mid bits, or fewer than two top bits: no plan."""
+    L = 18
+    np.asarray(inputs.disorder(L, 1.0, 1), dtype=np.float64).tofile(tmp_path / "h.bin")
+    for KS in (4, 15, 17):
+        r = subprocess.run([checker4, str(L), str(KS), "0.0", str(tmp_path)],
+                           capture_output=True, text=True)
+        assert r.returncode == 4 and "does not apply" in r.stdout
