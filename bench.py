@@ -252,9 +252,9 @@ def hv_kernel_name(L):
     on = (e == "1" and L >= 22) if e is not None else L >= 24
     if not on:
         return "k_matvec<float> (block form)"
-    if os.environ.get("HS_SB4") == "0":
-        return "k_sbhv<float, MODE_HV> (ten-low-bit superblock form)"
-    return "k_sb4<float, MODE_HV> (four-low-bit superblock form, one lane per sub-block)"
+    if os.environ.get("HS_SB4") == "1":
+        return "k_sb4<float, MODE_HV> (four-low-bit superblock form, one lane per sub-block)"
+    return "k_sbhv<float, MODE_HV> (ten-low-bit superblock form, one warp per sub-block)"
 
 
 def hv_roofline(torch, hs, L, stream):

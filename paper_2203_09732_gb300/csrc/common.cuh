@@ -27,6 +27,10 @@
 
 #include "../../include/hs.h"
 
+// hv_sb.cu: whether the four-low-bit superblock form (sb4.cuh) serves products
+// and MINRES pass A of precision dt where its plan applies
+bool hs_want_sb4(hs_dtype dt);
+
 namespace hs {
 
 constexpr int LMAX = 32;

@@ -148,12 +148,13 @@ static hs_status prep_smem(hs_handle* hd, K kern, size_t bytes) {
 
 hs_status launch_matvec(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted) {
   {
-    // superblock form: the FP32 default from L = 24 on (1.2-1.3x faster than
-    // the block form there); in FP64 the FP64 pipe bounds both forms and the
-    // block form is faster. HS_HV_SB=0 turns it off, =1 uses it for both
-    // precisions wherever a plan was built (L >= 22).
+    // superblock forms from L = 24 on: in FP32 the ten-low-bit form (1.2-1.3x
+    // faster than the block form there), in FP64 the four-low-bit form (the
+    // FP64 pipe bounds every form; it does the fewest FP64 operations).
+    // HS_HV_SB=0 turns them off, =1 uses them wherever a plan was built
+    // (L >= 22).
     const char* e = getenv("HS_HV_SB");
-    const bool on = e ? e[0] == '1' : (dt == HS_F32 && hd->L >= 24);
+    const bool on = e ? e[0] == '1' : hd->L >= 24;
     if (on) {
       bool used = false;
       hs_status st = launch_matvec_sb(hd, x, y, dt, shifted, &used);

@@ -100,10 +100,19 @@ namespace sb4 {
 constexpr int NT4_F = 512;   // FP32: two CTAs of 512 threads per SM
 constexpr int NT4_D = 256;   // FP64: more registers per thread
 
-template <typename T>
-auto kernel4() {
-  if constexpr (sizeof(T) == 8) return k_sb4<double, NT4_D, 2, 4, sb::MODE_HV>;
-  else return k_sb4<float, NT4_F, 2, 4, sb::MODE_HV>;
+// The kernel for a plan: the mid loop unrolled for the library's windows
+// (10 mid bits in FP32, 9 in FP64), a run-time loop for other windows.
+template <typename T, int MODE>
+using K4 = void (*)(Geo4, const T*, T*, const double*, int, sb::MinresArgs);
+template <typename T, int MODE>
+K4<T, MODE> kernel4_for(int km) {
+  if constexpr (sizeof(T) == 8) {
+    if (km == 9) return k_sb4<double, NT4_D, 2, 4, MODE, 9>;
+    return k_sb4<double, NT4_D, 2, 4, MODE, 0>;
+  } else {
+    if (km == 10) return k_sb4<float, NT4_F, 2, 4, MODE, 10>;
+    return k_sb4<float, NT4_F, 2, 4, MODE, 0>;
+  }
 }
 
 template <typename T>
@@ -165,7 +174,7 @@ static hs_status make_dev4(hs_handle* hd, int KS, DevPlan4** out) {
   }
   g.dscale = B.dscale;
   d->smem = smem_bytes4<T>(g.km, g.cmax);
-  auto kern = kernel4<T>();
+  auto kern = kernel4_for<T, sb::MODE_HV>(g.km);
   const int nt = sizeof(T) == 8 ? NT4_D : NT4_F;
   int nb = 0;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) ==
@@ -229,12 +238,20 @@ void sb_release(hs_handle* hd) {
   }
 }
 
-// HS_SB4=0 turns the four-low-bit form off (tests compare forms); it is used
-// wherever its plan applies.
-static bool want_sb4() {
+}  // namespace hs
+
+// The four-low-bit form is the FP64 default (measured at L = 24..28 it is the
+// fastest FP64 product: fewer FP64 additions of zeros than the ten-bit form,
+// and no gathers from global memory for most bonds, unlike the block form);
+// in FP32 the ten-bit form is faster. HS_SB4=1 / 0 selects it, or not, for
+// both precisions (tests compare forms).
+bool hs_want_sb4(hs_dtype dt) {
   const char* e = getenv("HS_SB4");
-  return !(e && e[0] == '0');
+  if (e) return e[0] == '1';
+  return dt == HS_F64;
 }
+
+namespace hs {
 
 hs_status launch_matvec_sb(hs_handle* hd, const void* x, void* y, hs_dtype dt, int shifted,
                            bool* used) {
@@ -242,14 +259,16 @@ hs_status launch_matvec_sb(hs_handle* hd, const void* x, void* y, hs_dtype dt, i
   {
     auto* d4 = static_cast<sb4::DevPlan4*>(hd->sb4_plan[dt == HS_F32 ? 0 : 1]);
     const size_t es = dt == HS_F32 ? sizeof(float) : sizeof(double);
-    if (want_sb4() && d4 && d4->ok && ((uintptr_t)x % es) == 0 && ((uintptr_t)y % es) == 0) {
+    if (hs_want_sb4(dt) && d4 && d4->ok && ((uintptr_t)x % es) == 0 && ((uintptr_t)y % es) == 0) {
       const sb::MinresArgs none{};
       if (dt == HS_F32)
-        sb4::kernel4<float>()<<<d4->grid, sb4::NT4_F, d4->smem, hd->stream>>>(
+        sb4::kernel4_for<float, sb::MODE_HV>(d4->geo.km)<<<d4->grid, sb4::NT4_F, d4->smem,
+                                                            hd->stream>>>(
             d4->geo, static_cast<const float*>(x), static_cast<float*>(y), hd->d_sigma, shifted,
             none);
       else
-        sb4::kernel4<double>()<<<d4->grid, sb4::NT4_D, d4->smem, hd->stream>>>(
+        sb4::kernel4_for<double, sb::MODE_HV>(d4->geo.km)<<<d4->grid, sb4::NT4_D, d4->smem,
+                                                             hd->stream>>>(
             d4->geo, static_cast<const double*>(x), static_cast<double*>(y), hd->d_sigma, shifted,
             none);
       count_launches(1);

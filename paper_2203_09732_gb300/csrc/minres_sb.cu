@@ -31,13 +31,18 @@ constexpr int NT_A4F = 512, NT_A4D = 256;
 template <typename T>
 constexpr int nt_a4() { return sizeof(T) == 8 ? NT_A4D : NT_A4F; }
 template <typename T>
-auto kern_A4() { return sb4::k_sb4<T, nt_a4<T>(), 2, 4, sb::MODE_MINRES>; }
-
-// HS_SB4=0 keeps pass A on the ten-low-bit layout (tests compare forms).
-bool want_sb4() {
-  const char* e = getenv("HS_SB4");
-  return !(e && e[0] == '0');
+using KA4 = void (*)(sb4::Geo4, const T*, T*, const double*, int, sb::MinresArgs);
+template <typename T>
+KA4<T> kern_A4(int km) {
+  if constexpr (sizeof(T) == 8) {
+    if (km == 9) return sb4::k_sb4<T, nt_a4<T>(), 2, 4, sb::MODE_MINRES, 9>;
+  } else {
+    if (km == 10) return sb4::k_sb4<T, nt_a4<T>(), 2, 4, sb::MODE_MINRES, 10>;
+  }
+  return sb4::k_sb4<T, nt_a4<T>(), 2, 4, sb::MODE_MINRES, 0>;
 }
+
+
 template <typename T, int PC, int MODE>
 auto kern_R() { return sb::k_sbrows<T, PC, MODE, NT_R>; }
 
@@ -66,10 +71,10 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
   if (!d || !d->ok) return HS_OK;
   const sb::Geo& g = d->geo;
   auto* d4 = static_cast<sb4::DevPlan4*>(hd->sb4_plan[ti]);
-  const bool use4 = want_sb4() && d4 && d4->ok;
+  const bool use4 = hs_want_sb4(sizeof(T) == 8 ? HS_F64 : HS_F32) && d4 && d4->ok;
   const size_t smA = use4 ? d4->smem : d->smem;
   const size_t smR = sb::rows_smem_bytes<T>(1 << g.k);
-  const int gA = use4 ? grid_of(hd, kern_A4<T>(), nt_a4<T>(), smA, d4->geo.npairs)
+  const int gA = use4 ? grid_of(hd, kern_A4<T>(d4->geo.km), nt_a4<T>(), smA, d4->geo.npairs)
                       : grid_of(hd, kern_A<T>(), NT_A, smA, g.npairs);
   const int gI = grid_of(hd, kern_R<T, PC, sb::ROWS_INIT>(), NT_R, smR, g.npairs);
   const int gB = grid_of(hd, kern_R<T, PC, sb::ROWS_B>(), NT_R, smR, g.npairs);
@@ -104,7 +109,8 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
       mB.counter = hd->d_counter + 2;
       for (int it = 0; it < SB_CHUNK; ++it) {
         if (use4)
-          kern_A4<T>()<<<gA, nt_a4<T>(), smA, cs>>>(d4->geo, nullptr, nullptr, hd->d_sigma, 1, mA);
+          kern_A4<T>(d4->geo.km)<<<gA, nt_a4<T>(), smA, cs>>>(d4->geo, nullptr, nullptr,
+                                                              hd->d_sigma, 1, mA);
         else
           kern_A<T>()<<<gA, NT_A, smA, cs>>>(g, nullptr, nullptr, hd->d_sigma, 1, mA);
         kern_R<T, PC, sb::ROWS_B>()<<<gB, NT_R, smR, cs>>>(g, nullptr, mB, 0.0, 0, hd->d_sigma);

@@ -8,7 +8,9 @@
 // lane can own a whole sub-block in registers. In shared memory every
 // sub-block of the CTA's superblock pair {T, T ^ top} has a slot of 8
 // elements at index m (slot address m * 8, whatever the class), so the
-// neighbours of a row are found by bit arithmetic on m:
+// neighbours of a row are found by bit arithmetic on m (the slot's elements
+// 0..3 and 4..7 live in two arrays of 16-byte entries, at the swizzled index
+// swz(m), see below):
 //   low interior  (j, j+1), j < 3        : same slot, another row (fixed per class);
 //   cut (3, 4)                           : slot m ^ 1, row of p ^ 8 (fixed per class);
 //   mid interior  (j, j+1), 4 <= j < KS-1 : slot m ^ (3 << (j-4)), same row;
@@ -19,6 +21,15 @@
 // The per-class row maps are compile-time constants (class template W), so
 // the row pass is vector loads of whole slots, adds and selects; the work list
 // of a superblock is sorted by class so that a warp's lanes share the class.
+//
+// Bank conflicts: a 16-byte load by a warp is served 8 lanes at a time, one
+// pass if the 8 entries fall in distinct 16-byte bank groups (index mod 8).
+// swz() below is linear over XOR and a bijection, so swz(m ^ c) =
+// swz(m) ^ swz(c): if the 8 lanes of a group have distinct swz(m) mod 8, so
+// do their neighbours m ^ c for every bond. The host deals each class run of
+// the work list so that every aligned group of 8 lanes has distinct
+// swz(m) mod 8 where the run allows it, and a lane whose bond is parallel
+// reads the zero entry of its own bank group.
 #pragma once
 #include "sb.cuh"
 
@@ -29,6 +40,20 @@ constexpr int K = 4;            // low bits
 constexpr int SLOT = 8;         // slot length (C(4, w) <= 6 rows)
 constexpr int KM_MAX = 10;      // mid bits: 1024 slots per superblock
 constexpr int WQ_MAX = sb::WQ_MAX;
+
+// Swizzled slot index: the low three bits of m mixed with bits 2..7 (a
+// bijection on [0, 2^km), linear over XOR).
+__host__ __device__ constexpr int swz(int m) { return m ^ ((m >> 2) & 7) ^ ((m >> 5) & 7); }
+constexpr int ZERO_ENT = 8;        // zero entries after the slots, one per bank group
+
+// Shared-memory slot arrays of a CTA, in 16-byte entries of 4 elements:
+// [lo rows of superblock 0 | lo rows of superblock 1 | hi rows of 0 | hi of 1],
+// each array 2^km + ZERO_ENT entries (the last ZERO_ENT are zero). Element offset of
+// row r of slot m of superblock 0 (superblock 1: + arr_elems(km)).
+__host__ __device__ constexpr int arr_elems(int km) { return ((1 << km) + ZERO_ENT) * 4; }
+__host__ __device__ constexpr int slot_elem(int km, int m, int r) {
+  return (r >= 4 ? 2 * arr_elems(km) : 0) + swz(m) * 4 + (r & 3);
+}
 
 // Low patterns of class w in ascending order.
 __host__ __device__ constexpr int cls_size(int w) {
@@ -108,20 +133,53 @@ inline bool build_plan4(int L, const double* h, int KS, HostPlan4* P) {
       P->dmid_d[m] = s.dmid;
       P->dmid_f[m] = (float)s.dmid;
     }
-    // by class w (descending popcount of m), then m: a warp's lanes share w
-    std::stable_sort(valid.begin(), valid.end(), [](int a, int b) {
-      return sb::popc_host((uint32_t)a) > sb::popc_host((uint32_t)b);
-    });
+    // by class w (descending popcount of m); within a class run, dealt in
+    // rounds of 8 with distinct swz(m) mod 8 (the fullest bank groups first),
+    // so that the lanes of an aligned group of 8 hit distinct bank groups
+    std::vector<uint16_t> dealt;
+    for (int pc = km; pc >= 0; --pc) {
+      std::vector<std::vector<int>> bk(8);
+      int left = 0;
+      for (int m : valid)
+        if (sb::popc_host((uint32_t)m) == pc) {
+          bk[swz(m) & 7].push_back(m);
+          ++left;
+        }
+      std::vector<size_t> at(8, 0);
+      while (left) {
+        int ord[8] = {0, 1, 2, 3, 4, 5, 6, 7};
+        std::stable_sort(ord, ord + 8, [&](int a, int b) {
+          return bk[a].size() - at[a] > bk[b].size() - at[b];
+        });
+        int took = 0;
+        for (int q = 0; q < 8 && took < 8; ++q)
+          if (at[ord[q]] < bk[ord[q]].size()) {
+            dealt.push_back((uint16_t)bk[ord[q]][at[ord[q]]++]);
+            ++took;
+            --left;
+          }
+        // fewer than 8 bank groups left: fill the group from the fullest
+        while (took < 8 && left) {
+          int f = 0;
+          for (int q = 1; q < 8; ++q)
+            if (bk[q].size() - at[q] > bk[f].size() - at[f]) f = q;
+          dealt.push_back((uint16_t)bk[f][at[f]++]);
+          ++took;
+          --left;
+        }
+      }
+    }
     P->order_off[wq] = (int)P->order.size();
     P->nvalid[wq] = (int)valid.size();
-    for (int m : valid) P->order.push_back((uint16_t)m);
-    // flat row -> slot element, in rank order (ascending m, then r)
+    P->order.insert(P->order.end(), dealt.begin(), dealt.end());
+    // flat row -> element offset in the CTA's slot arrays (superblock 0; add
+    // one array length for superblock 1), in rank order (ascending m, then r)
     P->slot_off[wq] = (int)P->slotmap.size();
     int rows = 0;
     for (int m = 0; m < nm; ++m) {
       const int w = wq - sb::popc_host((uint32_t)m);
       if (w < 0 || w > K) continue;
-      for (int r = 0; r < cls_size(w); ++r) P->slotmap.push_back((uint16_t)(m * SLOT + r));
+      for (int r = 0; r < cls_size(w); ++r) P->slotmap.push_back((uint16_t)slot_elem(km, m, r));
       rows += cls_size(w);
     }
     if (rows != (int)sb::binom64(KS, wq)) return *P = HostPlan4{}, false;
@@ -155,50 +213,49 @@ inline bool build_plan4(int L, const double* h, int KS, HostPlan4* P) {
 #define SB4_HD inline
 #endif
 
-// Copy N (4 or 8) elements of an 8-aligned slot.
-template <typename T, int N>
-SB4_HD void ld_slot(const T* p, T (&v)[SLOT]) {
+// Load one 16-byte-aligned entry of 4 elements.
+template <typename T>
+SB4_HD void ld4(const T* p, T* v) {
 #ifdef __CUDA_ARCH__
   if constexpr (sizeof(T) == 4) {
-    const float4 a = reinterpret_cast<const float4*>(p)[0];
+    const float4 a = *reinterpret_cast<const float4*>(p);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    if constexpr (N > 4) {
-      const float4 b = reinterpret_cast<const float4*>(p)[1];
-      v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    }
   } else {
-#pragma unroll
-    for (int q = 0; q < N / 2; ++q) {
-      const double2 a = reinterpret_cast<const double2*>(p)[q];
-      v[2 * q] = a.x; v[2 * q + 1] = a.y;
-    }
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
   }
 #else
-  for (int q = 0; q < N; ++q) v[q] = p[q];
+  for (int q = 0; q < 4; ++q) v[q] = p[q];
 #endif
 }
 
-// One sub-block for one lane: the C(4, W) rows of slot m of superblock s.
+// One sub-block for one lane: the C(4, W) rows of slot m.
 struct LaneIn {
   int m;              // mid pattern
   uint32_t b0;        // bit 0 of m
   uint32_t top;       // top bit of this superblock's T
   int km;
-  int nmidb;          // km - 1 mid interior bonds
 };
 
-// y = (H - sigma) x for the rows of one sub-block. xs: this superblock's
-// slots; xp: the partner superblock's slots (nullptr: no partner); g: the
-// flat G sums from the sub-block's first row; dl: the class table for
-// (top, b0); u = dmid + dT - sigma + Ising of bond (KS-1, KS); y: output from
-// the sub-block's first row. Returns sum_r x_r y_r.
-template <typename T, int W>
-SB4_HD T sb4_rows(const LaneIn& in, const T* xs, const T* xp, const T* g, const T* dl, T u,
-                  T* y) {
+// y = (H - sigma) x for the rows of one sub-block. xs: this superblock's lo
+// array (its hi array follows 2 arr_elems(km) elements later); xp: the
+// partner superblock's lo array (nullptr: no partner); g: the flat G sums from
+// the sub-block's first row, overwritten with y; dl: the class table for
+// (top, b0); u = dmid + dT - sigma + Ising of bond (KS-1, KS). KM: the number
+// of mid bits if known at compile time (0: in.km at run time). Returns
+// sum_r x_r y_r.
+template <typename T, int W, int KM>
+SB4_HD T sb4_rows(const LaneIn& in, const T* xs, const T* xp, T* g, const T* dl, T u) {
   constexpr int C = cls_size(W);
-  constexpr int NL = C > 4 ? 8 : 4;          // elements loaded per slot
+  constexpr bool HI = C > 4;                 // rows 4, 5 live in the hi array
+  const int km = KM ? KM : in.km;
+  const int nsl = 1 << km;
+  const int hi = 2 * arr_elems(km);
+  const int pm = swz(in.m);
   T x[SLOT], acc[SLOT], src[SLOT];
-  ld_slot<T, NL>(xs + in.m * SLOT, x);
+  ld4(xs + pm * 4, x);
+  if (HI) ld4(xs + hi + pm * 4, x + 4);
 #pragma unroll
   for (int r = 0; r < SLOT; ++r) acc[r] = T(0);
   // low interior bonds (j, j+1), j = 0, 1, 2: rows of the same slot
@@ -210,18 +267,29 @@ SB4_HD T sb4_rows(const LaneIn& in, const T* xs, const T* xp, const T* g, const 
       if (((p >> j) & 1) != ((p >> (j + 1)) & 1)) acc[r] += x[rank4(p ^ (3 << j))];
     }
   }
-  // mid interior bonds: slot m ^ (3 << j), same row
-  for (int j = 0; j < in.nmidb; ++j) {
-    if (((in.m >> j) ^ (in.m >> (j + 1))) & 1) {
-      ld_slot<T, NL>(xs + (in.m ^ (3 << j)) * SLOT, src);
+  // mid interior bonds (j, j+1) of m: slot m ^ (3 << j), same row; a parallel
+  // bond reads the zero entry of the bank group the antiparallel one would use
+  const int t = in.m ^ (in.m >> 1);
+  auto mid = [&](int j, int cj) {
+    const int idx = pm ^ cj;
+    const int at = ((t >> j) & 1) ? idx : nsl + (idx & 7);
+    ld4(xs + at * 4, src);
+    if (HI) ld4(xs + hi + at * 4, src + 4);
 #pragma unroll
-      for (int r = 0; r < C; ++r) acc[r] += src[r];
-    }
+    for (int r = 0; r < C; ++r) acc[r] += src[r];
+  };
+  if constexpr (KM > 0) {
+#pragma unroll
+    for (int j = 0; j < KM - 1; ++j) mid(j, swz(3 << j));
+  } else {
+    for (int j = 0; j < km - 1; ++j) mid(j, swz(3 << j));
   }
   // cut bond (3, 4): slot m ^ 1, row of p ^ 8 (classes W -+ 1)
   {
-    constexpr int NC = (W + 1 <= 4 && cls_size(W + 1) > 4) || (W >= 1 && cls_size(W - 1) > 4) ? 8 : 4;
-    ld_slot<T, NC>(xs + (in.m ^ 1) * SLOT, src);
+    constexpr bool CH = (W + 1 <= 4 && cls_size(W + 1) > 4) || (W >= 1 && cls_size(W - 1) > 4);
+    const int idx = pm ^ swz(1);
+    ld4(xs + idx * 4, src);
+    if (CH) ld4(xs + hi + idx * 4, src + 4);
 #pragma unroll
     for (int r = 0; r < C; ++r) {
       const int p = pat(W, r);
@@ -232,8 +300,9 @@ SB4_HD T sb4_rows(const LaneIn& in, const T* xs, const T* xp, const T* g, const 
   }
   // wrap bond (L-1, 0): the partner superblock's slot m, row of p ^ 1
   if (xp) {
-    constexpr int NW = (W + 1 <= 4 && cls_size(W + 1) > 4) || (W >= 1 && cls_size(W - 1) > 4) ? 8 : 4;
-    ld_slot<T, NW>(xp + in.m * SLOT, src);
+    constexpr bool WH = (W + 1 <= 4 && cls_size(W + 1) > 4) || (W >= 1 && cls_size(W - 1) > 4);
+    ld4(xp + pm * 4, src);
+    if (WH) ld4(xp + hi + pm * 4, src + 4);
 #pragma unroll
     for (int r = 0; r < C; ++r) {
       const int p = pat(W, r);
@@ -242,38 +311,76 @@ SB4_HD T sb4_rows(const LaneIn& in, const T* xs, const T* xp, const T* g, const 
       acc[r] += (b0p != in.top) ? v : T(0);
     }
   }
-  // whole-superblock shifts, then the row
+  // whole-superblock shifts, then the row (written over its G entry)
   T dot = T(0);
 #pragma unroll
   for (int r = 0; r < C; ++r) {
     const T a = acc[r] + g[r];
     const T d = dl[r] + u;
     const T yv = d * x[r] + T(0.5) * a;
-    y[r] = yv;
+    g[r] = yv;
     dot += x[r] * yv;
   }
   return dot;
 }
 
-template <typename T>
-SB4_HD T sb4_rows_any(int w, const LaneIn& in, const T* xs, const T* xp, const T* g, const T* dl,
-                      T u, T* y) {
+template <typename T, int KM>
+SB4_HD T sb4_rows_any(int w, const LaneIn& in, const T* xs, const T* xp, T* g, const T* dl, T u) {
   switch (w) {
-    case 0: return sb4_rows<T, 0>(in, xs, xp, g, dl, u, y);
-    case 1: return sb4_rows<T, 1>(in, xs, xp, g, dl, u, y);
-    case 2: return sb4_rows<T, 2>(in, xs, xp, g, dl, u, y);
-    case 3: return sb4_rows<T, 3>(in, xs, xp, g, dl, u, y);
-    default: return sb4_rows<T, 4>(in, xs, xp, g, dl, u, y);
+    case 0: return sb4_rows<T, 0, KM>(in, xs, xp, g, dl, u);
+    case 1: return sb4_rows<T, 1, KM>(in, xs, xp, g, dl, u);
+    case 2: return sb4_rows<T, 2, KM>(in, xs, xp, g, dl, u);
+    case 3: return sb4_rows<T, 3, KM>(in, xs, xp, g, dl, u);
+    default: return sb4_rows<T, 4, KM>(in, xs, xp, g, dl, u);
   }
 }
 
 // Flat pass over the rows of one superblock H (x rows xs[0, C)): G[i] = sum of
 // x over its high interior flips and its (KS-1, KS) flip; thread t of nt takes
-// rows t, t + nt, ..., U at a time so that U loads per bond are in flight.
-// (The same sums as sb::sb_phase1.)
+// rows t, t + nt, ..., U at a time so that U loads per bond are in flight (the
+// sums of sb::sb_phase1, with the bounds test only in the last round).
 template <typename T, int U>
 SB4_HD void sb4_phase1(const T* xs, const sb::Sup& H, T* G, int t, int nt) {
-  sb::sb_phase1<T, U>(xs, H, G, t, nt);
+  const int C = (int)H.C;
+  const int nh = (int)((H.meta >> 8) & 0xFF);
+  const int ka = (int)H.ka, kb = (int)H.kb;
+  const T* xk = xs + H.kd;
+  int i0 = t;
+  for (; i0 + (U - 1) * nt < C; i0 += U * nt) {
+    T g[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nt;
+      g[u] = (i >= ka && i < kb) ? xk[i] : T(0);
+    }
+    // four bonds at a time: 4 U independent loads in flight per thread
+    int q = 0;
+    for (; q + 4 <= nh; q += 4) {
+      T v[4][U];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const T* b = xs + H.hd[q + e] + i0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[e][u] = b[u * nt];
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int u = 0; u < U; ++u) g[u] += v[e][u];
+    }
+    for (; q < nh; ++q) {
+      const T* b = xs + H.hd[q] + i0;
+#pragma unroll
+      for (int u = 0; u < U; ++u) g[u] += b[u * nt];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) G[i0 + u * nt] = g[u];
+  }
+  for (; i0 < C; i0 += nt) {
+    T g = (i0 >= ka && i0 < kb) ? xk[i0] : T(0);
+    for (int q = 0; q < nh; ++q) g += xs[H.hd[q] + i0];
+    G[i0] = g;
+  }
 }
 
 #undef SB4_HD

@@ -22,8 +22,8 @@ using namespace hs::sb4;
 template <typename T>
 static void run(const HostPlan4& P, const T* x, T* y, double sigma) {
   const sb::HostPlan& B = P.base;
-  const int km = B.km, nsl = 1 << km;
-  std::vector<T> X(2 * (size_t)nsl * SLOT), G(2 * (size_t)P.cmax);
+  const int km = B.km, nsl = 1 << km, AE = arr_elems(km);
+  std::vector<T> X(4 * (size_t)AE), G(2 * (size_t)P.cmax);
   const std::vector<T> dl = [&] {
     std::vector<T> v(P.dl_d.size());
     for (size_t i = 0; i < v.size(); ++i) v[i] = sizeof(T) == 8 ? (T)P.dl_d[i] : (T)P.dl_f[i];
@@ -35,6 +35,8 @@ static void run(const HostPlan4& P, const T* x, T* y, double sigma) {
     sh[0] = pr.x >= 0 ? B.sup[pr.x] : sb::Sup{};
     sh[1] = pr.y >= 0 ? B.sup[pr.y] : sb::Sup{};
     for (T& v : X) v = (T)NAN;
+    for (int a = 0; a < 4; ++a)
+      for (int e = 0; e < ZERO_ENT * 4; ++e) X[(size_t)a * AE + nsl * 4 + e] = T(0);
     for (T& v : G) v = (T)NAN;
     T uT[4];
     for (int t = 0; t < 4; ++t) {
@@ -46,9 +48,9 @@ static void run(const HostPlan4& P, const T* x, T* y, double sigma) {
       if (!sh[s].C) continue;
       const int wq = (int)(sh[s].meta & 0xFF);
       const uint16_t* map = P.slotmap.data() + P.slot_off[wq];
-      for (uint32_t i = 0; i < sh[s].C; ++i) X[(size_t)s * nsl * SLOT + map[i]] = x[sh[s].R + i];
+      for (uint32_t i = 0; i < sh[s].C; ++i) X[(size_t)s * AE + map[i]] = x[sh[s].R + i];
       for (int t = 0; t < NT; ++t)
-        sb::sb_phase1<T, 4>(x + sh[s].R, sh[s], G.data() + (size_t)s * P.cmax, t, NT);
+        sb4_phase1<T, 4>(x + sh[s].R, sh[s], G.data() + (size_t)s * P.cmax, t, NT);
     }
     const int nv0 = sh[0].C ? P.nvalid[sh[0].meta & 0xFF] : 0;
     const int nv1 = sh[1].C ? P.nvalid[sh[1].meta & 0xFF] : 0;
@@ -66,14 +68,18 @@ static void run(const HostPlan4& P, const T* x, T* y, double sigma) {
       in.b0 = (uint32_t)m & 1u;
       in.top = (hm >> 17) & 1u;
       in.km = km;
-      in.nmidb = km - 1;
       const T dm = sizeof(T) == 8 ? (T)P.dmid_d[m] : (T)P.dmid_f[m];
       const T uu = dm + uT[s * 2 + ((m >> (km - 1)) & 1)];
-      const T* xp = sh[1 - s].C ? X.data() + (size_t)(1 - s) * nsl * SLOT : nullptr;
+      const T* xp = sh[1 - s].C ? X.data() + (size_t)(1 - s) * AE : nullptr;
       const T* dlw = dl.data() + (((int)in.top * 2 + (int)in.b0) * 5 + w) * SLOT;
-      sb4_rows_any<T>(w, in, X.data() + (size_t)s * nsl * SLOT, xp,
-                      G.data() + (size_t)s * P.cmax + lo, dlw, uu, y + H.R + lo);
+      // the run-time mid loop and, for the library's windows, the unrolled one
+      T* gs = G.data() + (size_t)s * P.cmax + lo;
+      if (km == 10) sb4_rows_any<T, 10>(w, in, X.data() + (size_t)s * AE, xp, gs, dlw, uu);
+      else if (km == 9) sb4_rows_any<T, 9>(w, in, X.data() + (size_t)s * AE, xp, gs, dlw, uu);
+      else sb4_rows_any<T, 0>(w, in, X.data() + (size_t)s * AE, xp, gs, dlw, uu);
     }
+    for (int s = 0; s < 2; ++s)
+      for (uint32_t i = 0; i < sh[s].C; ++i) y[sh[s].R + i] = G[(size_t)s * P.cmax + i];
   }
 }
 

@@ -2,8 +2,8 @@
 matrix-free (H - sigma) x of Eq. (1) with the x tiles of two superblocks
 staged in shared memory, against the oracle's explicit sparse H and against
 the block form. Two superblock forms: four low bits with one lane per
-sub-block (sb4, the default; HS_SB4=1) and ten low bits with one warp per
-sub-block (HS_SB4=0)."""
+sub-block (sb4; the FP64 default, HS_SB4=1 forces it) and ten low bits with
+one warp per sub-block (the FP32 default, HS_SB4=0 forces it)."""
 import numpy as np
 import pytest
 
@@ -96,10 +96,11 @@ def test_superblock_unaligned_vectors(dtype, offset, form, monkeypatch):
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 def test_four_bit_form_sampled_rows_l28(dtype, monkeypatch):
     """L = 28 (40,116,600 rows), the size of the benchmark, through the
-    default FP32 path (sb4) and sb4 in FP64: 300 sampled rows computed one by
-    one from Eq. (1)."""
+    four-low-bit form in FP32 and FP64: 300 sampled rows computed one by one
+    from Eq. (1)."""
     hs = need_gpu()
     monkeypatch.setenv("HS_HV_SB", "1")
+    monkeypatch.setenv("HS_SB4", "1")
     L = 28
     h = inputs.disorder(L, 3.7, 0)
     n = inputs.dim(L)

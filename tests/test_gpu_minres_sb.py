@@ -1,6 +1,7 @@
 """GPU parity of the superblock MINRES form (Algorithm 2 on the superblock
-layout: pass A = the superblock H x with the alpha dot (four-low-bit form by
-default, ten-bit form with HS_SB4=0), pass B = q_{k+1},
+layout: pass A = the superblock H x with the alpha dot (ten-low-bit form in
+FP32 and four-low-bit form in FP64 by default; HS_SB4 forces one), pass B =
+q_{k+1},
 beta_{k+1}, the Givens rotation and the d/x update of the previous iteration).
 It is the default from L = 24 on; HS_MINRES_SB=1 makes it the first choice
 wherever a superblock plan exists, and HS_SB_PLANS=1 with HS_KLO=4 builds
