@@ -150,9 +150,10 @@ def parse():
                     help="skip the iteration-model solves (value then null)")
     ap.add_argument("--static-budget", action="store_true", dest="static_budget")
     ap.add_argument("--detail", default=None, help="write per-step records to this JSON file")
-    ap.add_argument("--only", choices=["hv", "minres"], default=None,
-                    help="profiling cases: only the H x timing at --L, or one capped MINRES "
-                         "solve (FP32 + refinement) of --minres-iters iterations at --L")
+    ap.add_argument("--only", choices=["hv", "minres", "forms"], default=None,
+                    help="profiling cases: only the H x timing at --L; one capped MINRES "
+                         "solve (FP32 + refinement) of --minres-iters iterations at --L; or the "
+                         "products and MINRES iterations of every row form at L = 24, 26, 28")
     ap.add_argument("--minres-iters", type=int, default=200, dest="minres_iters")
     return ap.parse_args()
 
@@ -725,12 +726,66 @@ def l16_batch(torch, hs, args):
             "minres_iters": sum(i["minres_iters"] for i in out)}
 
 
+def forms_table(torch, hs, inputs):
+    """Microseconds per product and per MINRES iteration for each row form
+    (block, ten-low-bit and four-low-bit superblock; HS_HV_SB and HS_SB4 select
+    them) at L = 24, 26, 28, FP32 and FP64, CUDA events on the current stream."""
+    out = {}
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e3
+
+    saved = {k: os.environ.get(k) for k in ("HS_HV_SB", "HS_SB4")}
+    try:
+        for L in (24, 26, 28):
+            with hs.Chain(L, inputs.disorder(L, L28_H, 0), sigma=0.0) as c:
+                for name, dt, reps in (("f32", torch.float32, 10), ("f64", torch.float64, 3)):
+                    x = torch.randn(c.n, dtype=dt, device="cuda")
+                    y = torch.empty_like(x)
+                    for form, env in (("block", ("0", "0")), ("sb10", ("1", "0")), ("sb4", ("1", "1"))):
+                        os.environ["HS_HV_SB"], os.environ["HS_SB4"] = env
+                        for _ in range(2):
+                            c.matvec(x, y, shifted=True)
+                        out[f"hv L={L} {name} {form}"] = timed(lambda: c.matvec(x, y, shifted=True), reps)
+                    del x, y
+                os.environ["HS_HV_SB"] = "1"
+                b = torch.randn(c.n, dtype=torch.float64, device="cuda")
+                for name, lo, hi in (("f32", 20, 120), ("f64", 10, 30)):
+                    for form in ("0", "1"):
+                        os.environ["HS_SB4"] = form
+                        if name == "f32":
+                            run = lambda k: c.minres_f32(b.float(), tol=0.0, kmax=k, allow_not_converged=True)
+                        else:
+                            run = lambda k: c.minres(b, tol=0.0, kmax=k, allow_not_converged=True)
+                        t_lo, t_hi = timed(lambda: run(lo), 1), timed(lambda: run(hi), 1)
+                        key = "sb4" if form == "1" else "sb10"
+                        out[f"minres L={L} {name} pass A {key}"] = (t_hi - t_lo) / (hi - lo)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return out
+
+
 def run_only(args):
     """Single-kernel cases for profiler captures."""
     import torch
 
     from paper_2203_09732_gb300 import hs, inputs
     torch.cuda.set_device(0)
+    if args.only == "forms":
+        print(json.dumps(forms_table(torch, hs, inputs)))
+        return
     if args.only == "hv":
         rf = hv_roofline(torch, hs, args.L, torch.cuda.current_stream())
         print(json.dumps({k: {"GB/s": v["bytes"] / v["seconds"] / 1e9, "us": v["seconds"] * 1e6}
