@@ -22,6 +22,7 @@ Modules:
   lanczos      Algorithm 1 (Sec. II) with full reorthogonalisation.
   twist        twist overlap z = <psi|U_twist|psi> (Sec. III).
   rng          SplitMix64 counter-based generator for the Lanczos start vector.
+  observables  entanglement entropy and level spacing ratio (Sec. IV B).
 
 Parity pins: every function is checked in ``tests/test_oracle_*.py`` against
 closed forms, a Kronecker-product construction in the full 2^L space, brute
