@@ -232,6 +232,30 @@ hs_status hs_twist_noalloc(int L, const double* psi_dev, int K, double* z_dev,
 hs_status hs_tridiag_eig(int k, const double* alpha, const double* beta, double* theta,
                          double* Y);
 
+/* Bipartite entanglement entropy S_i = -Tr rho_A log rho_A (natural logarithm)
+ * of the K real FP64 vectors psi_dev + i n, n = C(L, L/2), for the subsystem A
+ * of sites 1..L/2 (Sec. IV B). The vectors need not be normalised (rho_A is
+ * divided by its trace). rho_A is block diagonal in the number a of up spins
+ * of A; each block rho_a = Psi_a Psi_a^T (Psi_a: the C(L/2, a) x C(L/2, a)
+ * coefficient block) is formed on the device in FP64, its eigenvalues on the
+ * host (as hs_sym_eigvals, one host thread per block). S_host: K entropies.
+ * Device scratch: sum_a C(L/2, a)^2 doubles (320 MB at L = 28), taken from
+ * the handle's pool and returned. Synchronises the stream. */
+hs_status hs_entanglement(hs_handle* hd, const double* psi_dev, int K, double* S_host);
+
+/* Level spacing ratios of Sec. IV B: with the K eigenvalues sorted and
+ * d_k = E_{k+1} - E_k, r_k = min(d_k, d_{k-1}) / max(d_k, d_{k-1}) for the
+ * K - 2 interior levels (r_host, may be NULL; equal neighbouring gaps of zero
+ * give 1), and *mean_out their mean (may be NULL). K >= 3, finite values.
+ * Host-only. */
+hs_status hs_level_ratio(const double* evals_host, int K, double* r_host, double* mean_out);
+
+/* Host-only: eigenvalues w_host[n] (ascending) of the symmetric n x n matrix
+ * a_host (row-major; both triangles read, overwritten) by Householder
+ * reduction to tridiagonal form and implicit QL. The host step of
+ * hs_entanglement. */
+hs_status hs_sym_eigvals(int n, double* a_host, double* w_host);
+
 /* Limit the persistent MINRES solves of this handle to nsm SMs (0 = all).
  * Independent handles on separate streams, each with a share of the SMs, then
  * solve their systems concurrently (several disorder realisations at once).

@@ -26,13 +26,19 @@ hs_status tridiag_eig(int k, const double* alpha, const double* beta, double* th
     for (int i = 0; i < k; ++i) Z[(size_t)i * k + i] = 1.0;  // column-major
   }
   const double eps = std::numeric_limits<double>::epsilon();
+  // an off-diagonal entry is negligible relative to its neighbours on the
+  // diagonal, or below eps ||T|| (a perturbation no larger than the backward
+  // error of the whole reduction; without it a block of zero eigenvalues that
+  // carries rounding-level off-diagonals never splits)
+  double anorm = 0.0;
+  for (int i = 0; i < k; ++i) anorm = std::max(anorm, std::fabs(d[i]) + std::fabs(e[i]));
   for (int l = 0; l < k; ++l) {
     int iter = 0;
     while (true) {
       int m = l;
       for (; m + 1 < k; ++m) {
         const double scale = std::fabs(d[m]) + std::fabs(d[m + 1]);
-        if (std::fabs(e[m]) <= eps * scale) break;
+        if (std::fabs(e[m]) <= eps * scale || std::fabs(e[m]) <= eps * anorm) break;
       }
       if (m == l) break;
       if (++iter > 60) return HS_NOT_CONVERGED;

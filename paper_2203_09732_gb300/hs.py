@@ -27,7 +27,8 @@ FORM_SMEM, FORM_SUPERBLOCK, FORM_PERSISTENT, FORM_GRAPH = 1, 2, 3, 4
 SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "hs_set_sigma",
            "hs_extremal", "hs_unrank", "hs_rank", "hs_diag", "hs_matvec", "hs_minres",
            "hs_minres_f32", "hs_lanczos_eigs", "hs_eigs_host", "hs_twist", "hs_tridiag_eig",
-           "hs_kernel_launches", "hs_set_sm_budget", "hs_twist_noalloc"]
+           "hs_kernel_launches", "hs_set_sm_budget", "hs_twist_noalloc", "hs_entanglement",
+           "hs_level_ratio", "hs_sym_eigvals"]
 
 
 class MinresInfo(ctypes.Structure):
@@ -101,6 +102,9 @@ def load(path=LIB_PATH):
         "hs_kernel_launches": ([], ctypes.c_ulonglong),
         "hs_set_sm_budget": ([H, ctypes.c_int], ctypes.c_int),
         "hs_twist_noalloc": ([ctypes.c_int, c_vp, ctypes.c_int, c_vp, c_vp], ctypes.c_int),
+        "hs_entanglement": ([H, c_vp, ctypes.c_int, c_dp], ctypes.c_int),
+        "hs_level_ratio": ([c_dp, ctypes.c_int, c_dp, c_dp], ctypes.c_int),
+        "hs_sym_eigvals": ([ctypes.c_int, c_dp, c_dp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -132,6 +136,27 @@ def twist_noalloc(L, psi, z, stream=None):
 def kernel_launches():
     """Kernels launched by libhs.so in this process so far."""
     return int(load().hs_kernel_launches())
+
+
+def level_ratio(evals):
+    """hs_level_ratio (host-only): (ratios of the K - 2 interior levels, mean)."""
+    e = np.ascontiguousarray(evals, dtype=np.float64)
+    r = np.zeros(max(0, len(e) - 2))
+    mean = ctypes.c_double()
+    st = load().hs_level_ratio(_dp(e), len(e), _dp(r), ctypes.byref(mean))
+    if st != HS_OK:
+        raise HSError(st, "hs_level_ratio")
+    return r, mean.value
+
+
+def sym_eigvals(a):
+    """hs_sym_eigvals (host-only): ascending eigenvalues of a symmetric matrix."""
+    A = np.array(a, dtype=np.float64, order="C", copy=True)
+    w = np.zeros(A.shape[0])
+    st = load().hs_sym_eigvals(A.shape[0], _dp(A), _dp(w))
+    if st != HS_OK:
+        raise HSError(st, "hs_sym_eigvals")
+    return w
 
 
 def tridiag_eig(alpha, beta, vectors=True):
@@ -295,6 +320,18 @@ class Chain:
         if not (allow_not_converged and st == HS_NOT_CONVERGED):
             self._check(st, "hs_lanczos_eigs")
         return ev, vecs, res, info.as_dict()
+
+    def entanglement(self, psi):
+        """Bipartite entanglement entropy of the rows of psi (K x n, FP64), A =
+        sites 1..L/2 (hs_entanglement)."""
+        t = self.torch
+        psi = psi.reshape(-1, self.n)
+        if not (psi.is_cuda and psi.dtype == t.float64 and psi.is_contiguous()):
+            raise ValueError("psi must be a contiguous CUDA float64 tensor")
+        S = np.zeros(psi.shape[0])
+        self._check(self._lib.hs_entanglement(self._hd, _ptr(psi), psi.shape[0], _dp(S)),
+                    "hs_entanglement")
+        return S
 
     def twist(self, psi):
         t = self.torch

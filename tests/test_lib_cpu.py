@@ -79,3 +79,39 @@ def test_binding_fails_loudly_without_library(tmp_path):
         ROOT, str(tmp_path / "missing.so"))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert "raised" in r.stdout and "missing" in r.stdout
+
+
+def test_level_ratio_matches_oracle(lib):
+    """hs_level_ratio (host-only) against the oracle's r_k, on random levels,
+    an unsorted input and the equal-spacing case."""
+    from oracle import observables as ob
+    from paper_2203_09732_gb300 import hs
+    rng = np.random.default_rng(5)
+    for K in (3, 4, 17, 50):
+        e = rng.normal(size=K)
+        r, mean = hs.level_ratio(e)
+        ref = ob.level_spacing_ratios(e)
+        assert np.allclose(r, ref, rtol=0, atol=1e-15) and abs(mean - ref.mean()) < 1e-15
+    r, mean = hs.level_ratio(np.arange(6.0))
+    assert np.all(r == 1.0) and mean == 1.0
+    with pytest.raises(hs.HSError):
+        hs.level_ratio([0.0, 1.0])
+
+
+def test_sym_eigvals_matches_numpy(lib):
+    """The host step of hs_entanglement: Householder + implicit QL eigenvalues
+    of symmetric matrices against numpy's eigvalsh (random, rank-deficient like
+    a reduced density matrix, diagonal, 1 x 1)."""
+    from paper_2203_09732_gb300 import hs
+    rng = np.random.default_rng(7)
+    for n in (1, 2, 3, 10, 70, 200):
+        A = rng.normal(size=(n, n))
+        A = A + A.T
+        w = hs.sym_eigvals(A)
+        assert np.abs(w - np.linalg.eigvalsh(A)).max() <= 1e-12 * max(1.0, np.abs(A).sum(axis=1).max())
+        B = rng.normal(size=(n, max(1, n // 3)))
+        R = B @ B.T
+        w = hs.sym_eigvals(R)
+        assert np.abs(w - np.linalg.eigvalsh(R)).max() <= 1e-12 * max(1.0, np.trace(R))
+    D = np.diag([3.0, -1.0, 2.0])
+    assert np.allclose(hs.sym_eigvals(D), [-1.0, 2.0, 3.0], atol=1e-15)
