@@ -232,6 +232,24 @@ hs_status hs_twist_noalloc(int L, const double* psi_dev, int K, double* z_dev,
 hs_status hs_tridiag_eig(int k, const double* alpha, const double* beta, double* theta,
                          double* Y);
 
+/* Derivatives of the twist overlaps of K eigenpairs with respect to the fields,
+ * by the adjoint of first-order perturbation theory. For each eigenpair
+ * (evals_host[i], psi_dev + i n) of H (real, non-degenerate; psi normalised by
+ * the call), with z = <psi|U_twist|psi> (Sec. III) and dH/dh_j = -Sz_j (Eq. (1)):
+ *   dz/dh_j = 2 lambda^T Sz_j psi,  (H - E) lambda = P (psi * u),  lambda _|_ psi,
+ * P = I - psi psi^T, u the diagonal of U_twist: one complex solve per pair, by
+ * the preconditioned MINRES of Algorithm 2 (FP64, row-norm preconditioner,
+ * shift E, relative tolerance tol; <= 0: 1e-10), whatever the number of sites.
+ * Outputs (host): z_host[2i], [2i+1] = Re, Im z_i (may be NULL);
+ * dz2_host[i L + j] = d|z_i|^2 / dh_{j+1}; dE_host[i L + j] = dE_i / dh_{j+1}
+ * = -<psi_i|Sz_{j+1}|psi_i> (Hellmann-Feynman; may be NULL); info: MINRES
+ * iterations summed over the solves (may be NULL). The handle's sigma is
+ * restored on return. Returns HS_NOT_CONVERGED if a solve reaches 50 n
+ * iterations (the gradients of the pairs done so far are valid). */
+hs_status hs_twist_grad(hs_handle* hd, const double* psi_dev, const double* evals_host, int K,
+                        double tol, double* z_host, double* dz2_host, double* dE_host,
+                        hs_minres_info* info);
+
 /* Bipartite entanglement entropy S_i = -Tr rho_A log rho_A (natural logarithm)
  * of the K real FP64 vectors psi_dev + i n, n = C(L, L/2), for the subsystem A
  * of sites 1..L/2 (Sec. IV B). The vectors need not be normalised (rho_A is

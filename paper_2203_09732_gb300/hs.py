@@ -28,7 +28,7 @@ SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "h
            "hs_extremal", "hs_unrank", "hs_rank", "hs_diag", "hs_matvec", "hs_minres",
            "hs_minres_f32", "hs_lanczos_eigs", "hs_eigs_host", "hs_twist", "hs_tridiag_eig",
            "hs_kernel_launches", "hs_set_sm_budget", "hs_twist_noalloc", "hs_entanglement",
-           "hs_level_ratio", "hs_sym_eigvals"]
+           "hs_level_ratio", "hs_sym_eigvals", "hs_twist_grad"]
 
 
 class MinresInfo(ctypes.Structure):
@@ -103,6 +103,8 @@ def load(path=LIB_PATH):
         "hs_set_sm_budget": ([H, ctypes.c_int], ctypes.c_int),
         "hs_twist_noalloc": ([ctypes.c_int, c_vp, ctypes.c_int, c_vp, c_vp], ctypes.c_int),
         "hs_entanglement": ([H, c_vp, ctypes.c_int, c_dp], ctypes.c_int),
+        "hs_twist_grad": ([H, c_vp, c_dp, ctypes.c_int, ctypes.c_double, c_dp, c_dp, c_dp,
+                           ctypes.POINTER(MinresInfo)], ctypes.c_int),
         "hs_level_ratio": ([c_dp, ctypes.c_int, c_dp, c_dp], ctypes.c_int),
         "hs_sym_eigvals": ([ctypes.c_int, c_dp, c_dp], ctypes.c_int),
     }
@@ -320,6 +322,25 @@ class Chain:
         if not (allow_not_converged and st == HS_NOT_CONVERGED):
             self._check(st, "hs_lanczos_eigs")
         return ev, vecs, res, info.as_dict()
+
+    def twist_grad(self, psi, evals, tol=1e-10):
+        """hs_twist_grad: for the K eigenpairs (rows of psi, evals), returns
+        (z [K] complex, d|z|^2/dh [K, L], dE/dh [K, L], MINRES info)."""
+        t = self.torch
+        psi = psi.reshape(-1, self.n)
+        if not (psi.is_cuda and psi.dtype == t.float64 and psi.is_contiguous()):
+            raise ValueError("psi must be a contiguous CUDA float64 tensor")
+        K = psi.shape[0]
+        ev = np.ascontiguousarray(evals, dtype=np.float64)
+        if ev.shape != (K,):
+            raise ValueError("evals must hold one eigenvalue per row of psi")
+        z = np.zeros(2 * K)
+        dz2 = np.zeros((K, self.L))
+        dE = np.zeros((K, self.L))
+        info = MinresInfo()
+        self._check(self._lib.hs_twist_grad(self._hd, _ptr(psi), _dp(ev), K, float(tol), _dp(z),
+                                            _dp(dz2), _dp(dE), ctypes.byref(info)), "hs_twist_grad")
+        return z[0::2] + 1j * z[1::2], dz2, dE, info.as_dict()
 
     def entanglement(self, psi):
         """Bipartite entanglement entropy of the rows of psi (K x n, FP64), A =
