@@ -69,11 +69,16 @@ typedef struct {
   int pad;
 } hs_minres_info;
 
-/* Solver forms (all run the same recurrence of Algorithm 2): vectors resident
- * in shared memory (chains up to L = 20 in FP64, 22 in FP32); superblock
- * passes (from L = 24 on); one persistent cooperative kernel with vectors in
- * global memory; per-pass kernels replayed from a CUDA graph. */
-enum { HS_FORM_SMEM = 1, HS_FORM_SUPERBLOCK = 2, HS_FORM_PERSISTENT = 3, HS_FORM_GRAPH = 4 };
+/* Solver forms (all run the recurrence of Algorithm 2): vectors resident in
+ * shared memory (chains up to L = 20 in FP64, 22 in FP32); superblock passes
+ * (from L = 24 on); one persistent cooperative kernel with vectors in global
+ * memory; per-pass kernels replayed from a CUDA graph; and the shared-memory
+ * form with one global reduction per iteration (the product taken of
+ * M^-1 p_k, p carried by the recurrence of q and replaced by a product every
+ * R steps, beta_{k+1}^2 expanded in sums known before alpha_k: equal in exact
+ * arithmetic, different in rounding). */
+enum { HS_FORM_SMEM = 1, HS_FORM_SUPERBLOCK = 2, HS_FORM_PERSISTENT = 3, HS_FORM_GRAPH = 4,
+       HS_FORM_SMEM1 = 5 };
 
 typedef struct {
   int steps;           /* Lanczos steps taken (k at exit)                         */

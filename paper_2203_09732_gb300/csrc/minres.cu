@@ -17,21 +17,13 @@
 #include <cstdio>
 #include <cstdlib>
 
-#include "minres_scalar.cuh"
-#include "rows.cuh"
+#include "minres_smem.cuh"
 
 namespace hs {
 
 // ---------------------------------------------------------------------------
 // Row passes shared by the per-pass kernels and the persistent kernel. Each
 // adds this thread's contribution to the pass's reduction into acc.
-template <typename T, int PC>
-__device__ __forceinline__ T row_m(const LowEntry& e, const Hdr& h, T& am) {
-  const uint32_t xc = cut_mask(e.packed, h);
-  am = diag_t<T>(e, h, xc);
-  return precond_t<PC, T>(am, naf_row(e.packed, h, xc));
-}
-
 template <typename T, int PC>
 __device__ __forceinline__ void rows_init(const Geo& g, const RowSmem<T>& s, double sigma,
                                           const T* __restrict__ bv, const MinresVecs& v, T& acc,
@@ -116,22 +108,6 @@ __device__ __forceinline__ void rows_B(const Geo& g, const RowSmem<T>& s, double
 // writes its partial sum, meets the others at a bounded grid barrier and then
 // adds all partials in the same fixed order, so every CTA holds identical
 // scalars without a second barrier.
-struct GridBar {
-  unsigned* count;
-  unsigned* gen;
-  int* err;
-};
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
 
 // Returns false in every thread if the wait hit its limit or another CTA
 // reported an error; the caller then leaves the kernel.
@@ -158,67 +134,6 @@ __device__ __forceinline__ bool grid_sync(const GridBar& gb, unsigned long long 
     s_ok = ok;
   }
   __syncthreads();
-  return s_ok != 0;
-}
-
-// Reduction + barrier in one step: CTA c publishes its two partial sums and the
-// reduction's generation number in slot c (release store, after a fence that
-// also publishes the CTA's other global writes); warp 0 of every CTA polls all
-// slots with acquire loads until each carries the generation, then adds them in
-// a fixed order (lane-strided sums and a fixed shuffle tree), so every CTA ends
-// with identical totals. Slots alternate between two buffers by generation
-// parity. The wait gives up after `limit` polls (HS_TIMEOUT).
-struct Slot {
-  double v0, v1;
-  unsigned gen;
-  unsigned pad[3];
-};
-
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ bool slot_reduce(Slot* slots, int G, unsigned gen, double v0, double v1,
-                                            double (&tot)[2], unsigned long long limit, int* err,
-                                            double* sbuf) {
-  __shared__ int s_ok;
-  Slot* buf = slots + (size_t)(gen & 1u) * G;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    buf[blockIdx.x].v0 = v0;
-    buf[blockIdx.x].v1 = v1;
-    __threadfence();
-    st_release_u32(&buf[blockIdx.x].gen, gen);
-  }
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    int ok = 1;
-    double a0 = 0.0, a1 = 0.0;
-    unsigned long long it = 0;
-    while (true) {
-      bool mine = true;
-      a0 = 0.0;
-      a1 = 0.0;
-      for (int c = lane; c < G; c += 32) {
-        if (ld_acquire_u32(&buf[c].gen) != gen) { mine = false; break; }
-        a0 += __ldcg(&buf[c].v0);
-        a1 += __ldcg(&buf[c].v1);
-      }
-      if (__all_sync(0xffffffffu, mine)) break;
-      if (++it > limit) { ok = 0; if (lane == 0) atomicExch(err, 1); break; }
-      if ((it & 255ull) == 0 && ld_relaxed_i32(err)) { ok = 0; break; }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-    }
-    ok = __all_sync(0xffffffffu, ok);
-    if (lane == 0) { sbuf[0] = a0; sbuf[1] = a1; s_ok = ok; }
-  }
-  __syncthreads();
-  tot[0] = sbuf[0];
-  tot[1] = sbuf[1];
   return s_ok != 0;
 }
 
@@ -323,211 +238,6 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_persist(Geo g, const T* _
 // global traffic per iteration is the gather of q_k for the off-diagonal
 // terms and the write of q_{k+1}. Same arithmetic, same order as the other
 // forms (rows_* above).
-
-// Rows of one block whose own segment (self and low-interior neighbours) is
-// read from shared memory xl; the other gathers come from global xg.
-template <typename T, int JM>
-__device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* xl, const T* dg,
-                                             const LowEntry* low, const Hdr& h, T (&xi)[JM],
-                                             T (&hx)[JM]) {
-  const int lane = threadIdx.x & 31;
-  const T* xb = xg + h.R;
-  T side[JM];
-#pragma unroll
-  for (int j = 0; j < JM; ++j) {
-    xi[j] = T(0);
-    side[j] = T(0);
-    hx[j] = T(0);
-    const int r = lane + 32 * j;
-    if (j < h.J && r < h.C) {
-      const LowEntry& e = low[h.off + r];
-      const uint32_t xc = cut_mask(e.packed, h);
-      xi[j] = xl[r];
-      const T c1 = (xc & 1u) ? ldx<T, true>(xb + h.bdelta + r) : T(0);
-      const T c2 = (xc & 2u) ? ldx<T, true>(xg + (h.Rwrap + e.wrap_r)) : T(0);
-      side[j] = c1 + c2;
-    }
-  }
-  constexpr int HG = 4;
-  for (int m0 = 0; m0 < h.nh; m0 += HG) {
-    T v[HG][JM];
-#pragma unroll
-    for (int mm = 0; mm < HG; ++mm) {
-      const bool on = m0 + mm < h.nh;
-      const T* xh = xb + (on ? hdr_hd(h, m0 + mm) : 0) + lane;
-#pragma unroll
-      for (int j = 0; j < JM; ++j)
-        v[mm][j] = (on && j < h.J && lane + 32 * j < h.C) ? ldx<T, true>(xh + 32 * j) : T(0);
-    }
-    // only the bonds that exist: the count is the same for the whole warp, so
-    // this skips FP64 adds of zero (the FP64 pipe bounds this pass)
-#pragma unroll
-    for (int mm = 0; mm < HG; ++mm)
-      if (m0 + mm < h.nh)
-#pragma unroll
-        for (int j = 0; j < JM; ++j) hx[j] += v[mm][j];
-  }
-#pragma unroll
-  for (int j = 0; j < JM; ++j) {
-    const int r = lane + 32 * j;
-    if (j < h.J && r < h.C) {
-      const LowEntry& e = low[h.off + r];
-      const uint32_t pk = e.packed;
-      T acc = hx[j] + side[j];
-      const int cnt = le_cnt(pk);
-      const uint32_t w0 = e.nbw[0], w1 = e.nbw[1], w2 = e.nbw[2];
-#pragma unroll
-      for (int m = 0; m < NB_MAX; ++m) {
-        const uint32_t wd = m < 4 ? w0 : (m < 8 ? w1 : w2);
-        if (m < cnt) acc += xl[(wd >> (8 * (m & 3))) & 0xFFu];
-      }
-      hx[j] = dg[r] * xi[j] + T(0.5) * acc;
-    }
-  }
-}
-
-// CTA-wide sum of two per-thread values; totals land in every lane of warp 0.
-// FP32 values are reduced in FP32 within warps (one FP64 add tree of 32 warp
-// sums follows); FP64 values go through shared memory so that one warp does the
-// FP64 additions (FP64 throughput on this part is a small fraction of FP32).
-template <typename T>
-__device__ __forceinline__ void cta_sum2(T a, T b, double* stmp, double& o0, double& o1) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if constexpr (sizeof(T) == 4) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) { stmp[2 * wid] = (double)a; stmp[2 * wid + 1] = (double)b; }
-    __syncthreads();
-    if (wid == 0) {
-      o0 = lane < nw ? stmp[2 * lane] : 0.0;
-      o1 = lane < nw ? stmp[2 * lane + 1] : 0.0;
-    }
-  } else {
-    stmp[threadIdx.x] = a;
-    stmp[blockDim.x + threadIdx.x] = b;
-    __syncthreads();
-    if (wid == 0) {
-      o0 = 0.0;
-      o1 = 0.0;
-      for (int i = lane; i < (int)blockDim.x; i += 32) {
-        o0 += stmp[i];
-        o1 += stmp[blockDim.x + i];
-      }
-    }
-  }
-  if (wid == 0) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      o0 += __shfl_xor_sync(0xffffffffu, o0, o);
-      o1 += __shfl_xor_sync(0xffffffffu, o1, o);
-    }
-  }
-}
-
-__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Slot reduction for grids of at most 256 CTAs, called by warp 0 with the
-// CTA's totals in (c0, c1): publish, poll every slot with independent relaxed
-// loads, one acquire fence, then a fixed-order sum (identical in every CTA).
-__device__ __forceinline__ bool slot_reduce_w0(Slot* slots, int G, unsigned gen, double c0,
-                                               double c1, double (&tot)[2],
-                                               unsigned long long limit, int* err) {
-  const int lane = threadIdx.x & 31;
-  Slot* buf = slots + (size_t)(gen & 1u) * G;
-  if (lane == 0) {
-    buf[blockIdx.x].v0 = c0;
-    buf[blockIdx.x].v1 = c1;
-    st_release_u32(&buf[blockIdx.x].gen, gen);   // orders the partials and, after the
-  }                                              // CTA barrier, the CTA's vector stores
-  int ok = 1;
-  unsigned long long it = 0;
-  while (true) {
-    unsigned gv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = lane + 32 * q;
-      gv[q] = c < G ? ld_relaxed_u32(&buf[c].gen) : gen;
-    }
-    bool mine = true;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) mine = mine && (gv[q] == gen);
-    if (__all_sync(0xffffffffu, mine)) break;
-    if (++it > limit) { ok = 0; if (lane == 0) atomicExch(err, 1); break; }
-    if ((it & 255ull) == 0 && ld_relaxed_i32(err)) { ok = 0; break; }
-  }
-  asm volatile("fence.acq_rel.gpu;" ::: "memory");
-  double a0 = 0.0, a1 = 0.0;
-  if (ok) {
-    double v0[8], v1[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int c = lane + 32 * q;
-      v0[q] = c < G ? __ldcg(&buf[c].v0) : 0.0;
-      v1[q] = c < G ? __ldcg(&buf[c].v1) : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) { a0 += v0[q]; a1 += v1[q]; }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-    }
-  }
-  tot[0] = a0;
-  tot[1] = a1;
-  return __all_sync(0xffffffffu, ok) != 0;
-}
-
-template <typename T>
-__host__ __device__ inline size_t smr_bytes(int nlow, int hdr_cap, int rows_cap, int nt) {
-  size_t b = sizeof(LowEntry) * (size_t)nlow + 128 * (size_t)hdr_cap;
-  b = (b + 15) & ~size_t(15);
-  b += 9 * sizeof(T) * (size_t)rows_cap;
-  b = (b + 15) & ~size_t(15);
-  return b + sizeof(double) * (sizeof(T) == 8 ? 2 * (size_t)nt : 64);
-}
-
-// Scalar recurrences of Algorithm 2 on one thread, with one reciprocal per
-// divisor (FP64 division and square root are slow here): same quantities as
-// givens_update.
-__device__ __forceinline__ void givens_fast(MinresState& S, double sumsq, double& ib) {
-  const double bn = sumsq >= 0.0 ? sqrt(sumsq) : NAN;        // beta_{k+1}
-  const double a = S.alpha, bk = S.beta;
-  const double cp = S.c_prev, sp = S.s_prev, dh = S.delta_hat, eps = S.eps;
-  const double delta = cp * dh + sp * a;                     // delta_k
-  const double gh = -sp * dh + cp * a;                       // hat gamma_k
-  const double gamma = sqrt(gh * gh + bn * bn);              // gamma_k
-  if (!isfinite(bn) || !isfinite(gamma)) {
-    S.status = HS_NONFINITE; S.done = 2; S.pending = 0;
-    return;
-  }
-  if (gamma == 0.0) {
-    S.status = HS_BREAKDOWN; S.done = 2; S.pending = 0;
-    return;
-  }
-  const double rg = 1.0 / gamma;
-  const double c = gh * rg, sn = bn * rg;                    // c_k, s_k
-  S.tau = c * S.phi;                                         // tau_k
-  S.phi = -sn * S.phi;                                       // phi_k
-  S.cq = rg * ib;                                            // 1 / (beta_k gamma_k)
-  S.cd1 = -delta * rg;
-  S.cd2 = -eps * rg;
-  S.pending = 1;
-  S.eps = sp * bn;                                           // epsilon_{k+1}
-  S.delta_hat = cp * bn;                                     // hat delta_{k+1}
-  S.beta_prev = bk; S.beta = bn;
-  S.c_prev = c; S.s_prev = sn;
-  S.k = S.k + 1;
-  ib = bn > 0.0 ? 1.0 / bn : 0.0;
-  if (fabs(S.phi) < S.tol_abs || bn == 0.0 || S.k > S.kmax) S.done = 1;
-}
 
 template <typename T, int PC, int JM, int NT>
 __global__ void __launch_bounds__(NT, 1) k_minres_smem(
@@ -880,7 +590,7 @@ static hs_status get_graph(hs_handle* hd, const MinresVecs& v, cudaGraphExec_t& 
 }
 
 // Contiguous block ranges per CTA with balanced row counts (cached per grid).
-static hs_status smr_plan(hs_handle* hd, int G, int** d_first, int* rows_cap, int* hdr_cap) {
+hs_status smr_plan(hs_handle* hd, int G, int** d_first, int* rows_cap, int* hdr_cap) {
   if (hd->smr_grid == G && hd->d_smr_first) {
     *d_first = hd->d_smr_first; *rows_cap = hd->smr_rows_cap; *hdr_cap = hd->smr_hdr_cap;
     return HS_OK;
@@ -1116,6 +826,26 @@ static int sb_choice(const hs_handle* hd) {
   return hd->L >= 24 ? 1 : 0;
 }
 
+// The one-reduction form (minres_pipe.cu) is the first choice for FP64 solves
+// with the identity or row-norm preconditioner while a CTA holds at most 1024
+// rows: there the second grid reduction of the two-reduction form is a third
+// of the iteration (measured at L = 14..18 on 152 SMs: 18.5 -> 14.2, 20.7 ->
+// 14.9 and 22.6 -> 18.9 us per iteration, the same iteration counts, true
+// residuals within 2x of the tolerance at 1e-12). With more rows per CTA the
+// extra FP64 vector work cancels the gain (L = 20 on 152 SMs, L = 16 on 6).
+// Not for Jacobi, whose ill-conditioned recurrence lets the carried p drift
+// (true residuals 10-100x the tolerance), nor by default for FP32, whose
+// drift costs the refinement sweeps more than the faster iterations win.
+// HS_MINRES_PIPE=1 makes it the first choice wherever it fits, =0 turns it off.
+static bool pipe_choice(const hs_handle* hd, bool f64, int pc) {
+  const char* e = getenv("HS_MINRES_PIPE");
+  if (e) return e[0] == '1';
+  if (!f64 || pc == 1) return false;
+  const int bud = hd->sm_budget.load(std::memory_order_relaxed);
+  const int G = std::max(1, std::min(hd->num_sms, bud > 0 ? bud : hd->num_sms));
+  return hd->n <= 1024LL * G;
+}
+
 template <typename T, int PC>
 static hs_status try_sb(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
                         long long kmax) {
@@ -1135,6 +865,10 @@ static hs_status solve_pc(hs_handle* hd, const T* b, T* x, double tol, long long
   int form = 0;
   const int sbc = sb_choice(hd);
   if (sbc == 2 && (st = try_sb<T, PC>(hd, b, v, tol, kmax)) != HS_CUDA) form = HS_FORM_SUPERBLOCK;
+  if (st == HS_CUDA && !force_graph() && !force_global() && pipe_choice(hd, sizeof(T) == 8, PC) &&
+      (st = minres_solve_pipe(hd, b, v, sizeof(T) == 8 ? HS_F64 : HS_F32, PC, tol, kmax)) !=
+          HS_CUDA)
+    form = HS_FORM_SMEM1;
   if (st == HS_CUDA && !force_graph() && !force_global() &&
       (st = solve_smem<T, PC>(hd, b, v, tol, kmax)) != HS_CUDA)
     form = HS_FORM_SMEM;

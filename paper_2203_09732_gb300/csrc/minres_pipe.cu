@@ -1,0 +1,393 @@
+// Preconditioned MINRES of Algorithm 2 (Appendix A) with one global reduction
+// per iteration, shared-memory resident like k_minres_smem (one CTA per SM,
+// each CTA's rows of every vector on chip; L <= 20).
+//
+// Algorithm 2 needs two global sums per iteration: alpha_k = q_k . p_k / beta_k^2
+// before q_{k+1} can be formed, and beta_{k+1}^2 = q_{k+1} . M q_{k+1} after it.
+// Here both come from one exchange, by two changes that leave the arithmetic
+// of exact arithmetic unchanged:
+//   * the product is applied to v_k = M^-1 p_k instead of to q_{k+1}, and p is
+//     carried by the three-term recurrence of q (H - sigma is linear):
+//       q_{k+1} = v_k / beta_k - a q_k - c q_{k-1},
+//       p_{k+1} = (H - sigma) v_k / beta_k - a p_k - c p_{k-1},
+//     a = alpha_k / beta_k, c = beta_k / beta_{k-1};
+//   * beta_{k+1}^2, the M-norm of q_{k+1} as formed above, is expanded in sums
+//     that exist before alpha_k is known:
+//       beta_{k+1}^2 = S2 / beta_k^2 + a^2 S4 + c^2 S6
+//                      - 2 a S1 / beta_k - 2 c S3 / beta_k + 2 a c S5,
+//     S1 = q_k.p_k, S2 = p_k.M^-1 p_k, S3 = p_k.q_{k-1}, S4 = q_k.M q_k,
+//     S5 = q_k.M q_{k-1}, S6 = q_{k-1}.M q_{k-1} (S4 of the step before). The
+//     expansion does not assume M-orthogonality of the computed q.
+// One iteration: the scalars of step k (alpha_k, beta_{k+1}, the Givens
+// rotation) from the sums on one thread; one pass over the rows: d_k and x_k,
+// (H - sigma) v_k (gathering v_k), q_{k+1}, p_{k+1}, v_{k+1} = M^-1 p_{k+1}, the
+// five sums of step k+1 and the store of v_{k+1}; then one reduction, which is
+// also the barrier that publishes v_{k+1}.
+//
+// Rounding makes p drift from (H - sigma) q; every R steps p_{k+1} is instead
+// formed as the product with q_{k+1} (that step publishes q_{k+1} first: one
+// extra barrier). Where the expansion cancels to rounding level (beta_{k+1}^2
+// below EXPANSION_FLOOR of its terms) the solve ends with HS_BREAKDOWN and
+// pad = PIPE_EXPANSION, and the caller solves again with the two-reduction form.
+#include <cstdlib>
+
+#include "minres_smem.cuh"
+
+namespace hs {
+
+namespace {
+
+constexpr int PIPE_NV = 5;           // S1..S5 (S6 is carried)
+constexpr int PIPE_EXPANSION = 1;    // MinresState.pad: the expansion was not trusted
+
+// Smallest beta_{k+1}^2 / mag (mag: the sum of the expansion's terms in
+// magnitude) that the expansion is trusted with: its relative error is about
+// u mag / beta_{k+1}^2, at most 1e-8 (FP64) or 6e-5 (FP32) above the floor.
+// Below it (in practice: a Krylov space that has run out, as for n <= 8 or a
+// right-hand side inside an invariant subspace) the solve is handed back.
+template <typename T>
+constexpr double EXPANSION_FLOOR = sizeof(T) == 8 ? 1e-8 : 1e-3;
+
+// Shared memory: low table, block headers, 11 row arrays, reduction staging.
+template <typename T>
+size_t smr1_bytes(int nlow, int hdr_cap, int rows_cap, int nt) {
+  size_t b = sizeof(LowEntry) * (size_t)nlow + 128 * (size_t)hdr_cap;
+  b = (b + 15) & ~size_t(15);
+  b += 11 * sizeof(T) * (size_t)rows_cap;
+  b = (b + 15) & ~size_t(15);
+  return b + sizeof(double) * PIPE_NV * (sizeof(T) == 8 ? (size_t)nt : 32);
+}
+
+template <typename T, int PC, int JM, int NT>
+__global__ void __launch_bounds__(NT, 1) k_minres_smem1(
+    Geo g, const T* __restrict__ bv, T* vg0, T* vg1, T* qg, T* xout, MinresState* st, double tol,
+    long long kmax, int rperiod, const double* d_sigma, SlotN* slots, int* err,
+    unsigned long long limit, const int* __restrict__ cta_first, int rows_cap) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ MinresState S;
+  __shared__ double s_sum[PIPE_NV + 1];   // S1..S5 of the current step, S6
+  __shared__ double s_cta[PIPE_NV];
+  __shared__ double s_c[3];               // 1/beta_k, a, c of the vector update
+  __shared__ double s_ib, s_ibp;          // 1/beta_k, 1/beta_{k-1}
+  __shared__ int s_ok;
+  LowEntry* low = reinterpret_cast<LowEntry*>(smem);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(g.low);
+    uint4* dst = reinterpret_cast<uint4*>(low);
+    for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  const int b0 = cta_first[blockIdx.x], nbk = cta_first[blockIdx.x + 1] - b0;
+  uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * g.nlow);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
+    for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
+  }
+  size_t off = sizeof(LowEntry) * g.nlow + 128 * (size_t)nbk;
+  off = (off + 15) & ~size_t(15);
+  T* Q0 = reinterpret_cast<T*>(smem + off);   // q_j in Q[j & 1]
+  T* Q1 = Q0 + rows_cap;
+  T* P0 = Q0 + 2 * rows_cap;                  // p_j in P[j & 1]
+  T* P1 = Q0 + 3 * rows_cap;
+  T* D0 = Q0 + 4 * rows_cap;                  // d_j in D[j & 1]
+  T* D1 = Q0 + 5 * rows_cap;
+  T* VL = Q0 + 6 * rows_cap;                  // v_k (own rows)
+  T* X = Q0 + 7 * rows_cap;
+  T* MV = Q0 + 8 * rows_cap;                  // M_ii
+  T* MI = Q0 + 9 * rows_cap;                  // 1 / M_ii
+  T* DG = Q0 + 10 * rows_cap;                 // a_ii - sigma
+  off += 11 * sizeof(T) * (size_t)rows_cap;
+  off = (off + 15) & ~size_t(15);
+  double* stmp = reinterpret_cast<double*>(smem + off);
+  const uint32_t Rbase = __ldg(&g.blocks[b0].R);
+  const double sigma = *d_sigma;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nact = min(nbk, NT / 32);         // warps that own blocks
+  __syncthreads();
+  auto each_block = [&](auto&& f) {
+    for (int lb = wid; lb < nbk; lb += NT / 32) {
+      const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+      f(h, h.R - Rbase);
+    }
+  };
+  const int G = gridDim.x;
+  unsigned gen = 0;
+  auto reduce = [&](const T (&a)[PIPE_NV]) -> bool {
+    cta_sumN<T, PIPE_NV>(a, nact, stmp, s_cta);
+    ++gen;
+    if (wid == 0) {
+      double t[PIPE_NV];
+      const bool okw = slot_reduceN_w0<PIPE_NV>(slots, G, gen, s_cta, t, limit, err);
+      if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < PIPE_NV; ++j) s_sum[j] = t[j];
+        s_ok = okw;
+      }
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
+  bool ok;
+  // q_1 = M^-1 b (x_0 = 0), q_0 = p_0 = 0, d_0 = d_{-1} = 0; q_1 is published
+  // for the first product
+  {
+    T a[PIPE_NV] = {};
+    each_block([&](const Hdr& h, uint32_t l0) {
+      for (int r = lane; r < h.C; r += 32) {
+        T am;
+        const T m = row_m<T, PC>(low[h.off + r], h, am);
+        const uint32_t i = h.R + r;
+        const uint32_t l = l0 + r;
+        const T b = bv[i];
+        a[1] += (m == T(0)) ? T(1) : T(0);
+        const T mi = m == T(0) ? T(0) : T(1) / m;
+        const T q = b * mi;
+        MV[l] = m; MI[l] = mi; DG[l] = am;
+        Q1[l] = q; qg[i] = q;
+        Q0[l] = T(0); P0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
+        a[0] += q * b;
+      }
+    });
+    ok = reduce(a);
+    if (ok && threadIdx.x == 0) {
+      init_state(S, s_sum[0], s_sum[1], tol, kmax, sigma);
+      s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
+      s_ibp = 1.0;                             // 1 / beta_0
+    }
+    __syncthreads();
+  }
+  // p_1 = (H - sigma) q_1, v_1 and the sums of step 1 (S3 = S5 = S6 = 0)
+  if (ok && S.done == 0) {
+    T a[PIPE_NV] = {};
+    each_block([&](const Hdr& h, uint32_t l0) {
+      T xi[JM], hx[JM];
+      block_hv_loc<T, JM>(qg, Q1 + l0, DG + l0, low, h, xi, hx);
+#pragma unroll
+      for (int j = 0; j < JM; ++j) {
+        const int r = lane + 32 * j;
+        if (j < h.J && r < h.C) {
+          const uint32_t l = l0 + r;
+          const T p = hx[j];
+          const T v = MI[l] * p;
+          P1[l] = p; VL[l] = v; vg1[h.R + r] = v;
+          a[0] += xi[j] * p;
+          a[1] += p * v;
+          a[3] += MV[l] * xi[j] * xi[j];
+        }
+      }
+    });
+    ok = reduce(a);
+    if (threadIdx.x == 0) s_sum[PIPE_NV] = 0.0;
+    __syncthreads();
+  }
+  while (ok && S.done == 0) {
+    // scalars of step k
+    if (threadIdx.x == 0) {
+      const double bk = S.beta, ib = s_ib;
+      const double S1 = s_sum[0], S2 = s_sum[1], S3 = s_sum[2], S4 = s_sum[3], S5 = s_sum[4];
+      const double S6 = s_sum[5];
+      const double alpha = S1 * ib * ib;                         // alpha_k
+      const double a = alpha * ib, c = bk * s_ibp;
+      const double b2 = S2 * ib * ib + a * a * S4 + c * c * S6 - 2.0 * a * S1 * ib -
+                        2.0 * c * S3 * ib + 2.0 * a * c * S5;   // beta_{k+1}^2
+      // the terms' magnitude: b2 carries a rounding error of about
+      // u mag, with u the unit roundoff of the vectors
+      const double mag = S2 * ib * ib + a * a * S4 + c * c * S6 + fabs(2.0 * a * S1 * ib) +
+                         fabs(2.0 * c * S3 * ib) + fabs(2.0 * a * c * S5);
+      s_c[0] = ib; s_c[1] = a; s_c[2] = c;
+      s_sum[5] = S4;
+      S.alpha = alpha;
+      if (!isfinite(alpha) || !isfinite(b2)) {
+        S.status = HS_NONFINITE; S.done = 2; S.pending = 0;
+      } else if (!(b2 > EXPANSION_FLOOR<T> * mag)) {
+        S.status = HS_BREAKDOWN; S.pad = PIPE_EXPANSION; S.done = 2; S.pending = 0;
+      } else {
+        double ibn = ib;
+        givens_fast(S, b2, ibn);
+        s_ibp = ib;
+        s_ib = ibn;
+      }
+    }
+    __syncthreads();
+    if (S.done == 2) break;
+    const long long kk = S.k - 1;               // the step just rotated
+    const bool doMV = S.done == 0;
+    const bool repl = doMV && rperiod > 0 && (kk % rperiod) == 0;
+    const bool odd = (kk & 1) != 0;
+    const T* Qk = odd ? Q1 : Q0;                // q_k
+    T* Qm = odd ? Q0 : Q1;                      // q_{k-1} -> q_{k+1}
+    const T* Pk = odd ? P1 : P0;                // p_k
+    T* Pm = odd ? P0 : P1;                      // p_{k-1} -> p_{k+1}
+    const T* Dm = odd ? D0 : D1;                // d_{k-1}
+    T* Dk = odd ? D1 : D0;                      // d_{k-2} -> d_k
+    const T* vgk = odd ? vg1 : vg0;             // v_k
+    T* vgn = odd ? vg0 : vg1;                   // v_{k+1}
+    const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
+    const T c1 = (T)s_c[0], c2 = (T)s_c[1], c3 = (T)s_c[2];
+    T a[PIPE_NV] = {};
+    each_block([&](const Hdr& h, uint32_t l0) {
+      // d_k = (q_k / beta_k - delta_k d_{k-1} - eps_k d_{k-2}) / gamma_k, x_k
+      for (int r = lane; r < h.C; r += 32) {
+        const uint32_t l = l0 + r;
+        const T d = cq * Qk[l] + cd1 * Dm[l] + cd2 * Dk[l];
+        Dk[l] = d;
+        X[l] += tau * d;
+      }
+      if (!doMV) return;
+      if (repl) {
+        for (int r = lane; r < h.C; r += 32) {
+          const uint32_t l = l0 + r;
+          const T q = c1 * VL[l] - c2 * Qk[l] - c3 * Qm[l];
+          Qm[l] = q;
+          qg[h.R + r] = q;
+        }
+        return;
+      }
+      T xi[JM], hx[JM];
+      block_hv_loc<T, JM>(vgk, VL + l0, DG + l0, low, h, xi, hx);   // xi = v_k
+      __syncwarp();                             // the block's reads of VL are done
+#pragma unroll
+      for (int j = 0; j < JM; ++j) {
+        const int r = lane + 32 * j;
+        if (j < h.J && r < h.C) {
+          const uint32_t l = l0 + r;
+          const T qo = Qk[l];
+          const T q = c1 * xi[j] - c2 * qo - c3 * Qm[l];
+          const T p = c1 * hx[j] - c2 * Pk[l] - c3 * Pm[l];
+          const T v = MI[l] * p;
+          Qm[l] = q; Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
+          const T mq = MV[l] * q;
+          a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
+        }
+      }
+    });
+    if (!doMV) {                                // the last d/x update only
+      __syncthreads();
+      if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
+      __syncthreads();
+      break;
+    }
+    if (repl) {
+      // publish q_{k+1}, then p_{k+1} = (H - sigma) q_{k+1}
+      if (!(ok = reduce(a))) break;
+      each_block([&](const Hdr& h, uint32_t l0) {
+        T xi[JM], hx[JM];
+        block_hv_loc<T, JM>(qg, Qm + l0, DG + l0, low, h, xi, hx);  // xi = q_{k+1}
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+          const int r = lane + 32 * j;
+          if (j < h.J && r < h.C) {
+            const uint32_t l = l0 + r;
+            const T qo = Qk[l];
+            const T q = xi[j];
+            const T p = hx[j];
+            const T v = MI[l] * p;
+            Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
+            const T mq = MV[l] * q;
+            a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
+          }
+        }
+      });
+    }
+    if (!(ok = reduce(a))) break;
+  }
+  __syncthreads();
+  each_block([&](const Hdr& h, uint32_t l0) {
+    for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
+  });
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
+    *st = S;
+  }
+}
+
+// Steps between replacements of p by a product: HS_MINRES_PIPE_R, else 20.
+// Measured at L = 14..18 (FP64, tolerance 1e-12, row norm): without
+// replacement the true residual ends 5-900x above the tolerance; R = 50 1.0-3.4x,
+// R = 20 1.0-1.9x (the two-reduction form 0.9-1.3x), at the same iteration
+// counts, wherever the two-reduction form reaches the tolerance; each
+// replacement costs one extra barrier.
+int replace_period() {
+  if (const char* e = getenv("HS_MINRES_PIPE_R")) return std::max(0, atoi(e));
+  return 20;
+}
+
+// HS_CUDA (no message) when the form does not apply: no room in shared memory,
+// no cooperative launch, or the expansion of beta^2 was not trusted (the caller
+// then solves with the two-reduction form).
+template <typename T, int PC, int JM, int NT>
+hs_status solve_v(hs_handle* hd, const T* b, const MinresVecs& v, double tol, long long kmax) {
+  const int bud = hd->sm_budget.load(std::memory_order_relaxed);
+  const int G = std::max(1, std::min(hd->num_sms, bud > 0 ? bud : hd->num_sms));
+  if (G > 256) return HS_CUDA;
+  int* first = nullptr;
+  int rows_cap = 0, hdr_cap = 0;
+  hs_status st = smr_plan(hd, G, &first, &rows_cap, &hdr_cap);
+  if (st != HS_OK) return st;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, hd->device);
+  const size_t sm = smr1_bytes<T>((int)hd->low.size(), hdr_cap, rows_cap, NT);
+  const size_t static_sm = sizeof(MinresState) + 24 * 8 + 64;
+  if (sm + static_sm > (size_t)optin) return HS_CUDA;
+  if (cudaFuncSetAttribute(k_minres_smem1<T, PC, JM, NT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+    cudaGetLastError();
+    return HS_CUDA;
+  }
+  Geo g = hd->geo();
+  int* err = reinterpret_cast<int*>(hd->d_counter + 10);
+  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_counter + 10, 0, sizeof(unsigned), hd->stream));
+  // generations start from zero for every solve
+  SlotN* slots = reinterpret_cast<SlotN*>(hd->d_partial);
+  HS_CUDA_TRY(hd, cudaMemsetAsync(slots, 0, 2 * sizeof(SlotN) * G, hd->stream));
+  const double* ds = hd->d_sigma;
+  MinresState* stp = hd->d_state;
+  unsigned long long limit = 1ull << 22;
+  if (const char* e = getenv("HS_BARRIER_LIMIT")) limit = strtoull(e, nullptr, 10);
+  int rp = replace_period();
+  T* vg0 = (T*)v.q0;
+  T* vg1 = (T*)v.q1;
+  T* qg = (T*)v.p;
+  T* xo = (T*)v.x;
+  void* args[] = {&g, (void*)&b, &vg0, &vg1, &qg, &xo, &stp, &tol, &kmax, &rp, (void*)&ds,
+                  &slots, &err, &limit, &first, &rows_cap};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_minres_smem1<T, PC, JM, NT>, dim3(G),
+                                              dim3(NT), args, sm, hd->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return HS_CUDA;
+  }
+  count_launches(1);
+  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
+                                  cudaMemcpyDeviceToHost, hd->stream));
+  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
+  const MinresState& S = *hd->h_state;
+  if (S.status == HS_BREAKDOWN && S.pad == PIPE_EXPANSION) return HS_CUDA;
+  return HS_OK;
+}
+
+template <typename T, int PC>
+hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, long long kmax) {
+  // blocks of at most 96 rows (k <= 8, every chain up to L = 20): 3 rows per
+  // lane; larger blocks 8 rows per lane and 256 threads (a few blocks per CTA
+  // at most, and no register spills in FP64)
+  if (hd->k <= 8) return solve_v<T, PC, 3, 512>(hd, b, v, tol, kmax);
+  return solve_v<T, PC, JMAX, 256>(hd, b, v, tol, kmax);
+}
+
+}  // namespace
+
+hs_status minres_solve_pipe(hs_handle* hd, const void* b, const MinresVecs& v, hs_dtype dt,
+                            int pc, double tol, long long kmax) {
+  if (dt == HS_F64) {
+    const double* bb = (const double*)b;
+    return pc == 0 ? solve_t<double, 0>(hd, bb, v, tol, kmax)
+         : pc == 1 ? solve_t<double, 1>(hd, bb, v, tol, kmax)
+                   : solve_t<double, 2>(hd, bb, v, tol, kmax);
+  }
+  const float* bb = (const float*)b;
+  return pc == 0 ? solve_t<float, 0>(hd, bb, v, tol, kmax)
+       : pc == 1 ? solve_t<float, 1>(hd, bb, v, tol, kmax)
+                 : solve_t<float, 2>(hd, bb, v, tol, kmax);
+}
+
+}  // namespace hs

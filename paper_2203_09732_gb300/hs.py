@@ -21,7 +21,7 @@ STATUS_NAMES = ["HS_OK", "HS_BAD_ARG", "HS_OOM", "HS_CUDA", "HS_NOT_CONVERGED", 
                 "HS_NONFINITE", "HS_TIMEOUT"]
 F32, F64 = 0, 1
 PRECOND = {"id": 0, "jacobi": 1, "row": 2}
-FORM_SMEM, FORM_SUPERBLOCK, FORM_PERSISTENT, FORM_GRAPH = 1, 2, 3, 4
+FORM_SMEM, FORM_SUPERBLOCK, FORM_PERSISTENT, FORM_GRAPH, FORM_SMEM1 = 1, 2, 3, 4, 5
 
 # every symbol include/hs.h declares
 SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "hs_set_sigma",

@@ -211,14 +211,18 @@ def test_barrier_timeout_reports_status(monkeypatch):
 @pytest.mark.parametrize("L", [12, 16])
 def test_solver_forms_agree(L, form, monkeypatch):
     """Every solver form (per-pass kernels under a CUDA graph, the
-    global-memory persistent form) against the default
+    global-memory persistent form) against the two-reduction
     shared-memory persistent form: the same row passes, so iteration counts
     agree to rounding drift and both solutions meet the tolerance."""
     hs = need_gpu()
+    # the two-reduction shared-memory form; the one-reduction form has its own
+    # tests (test_gpu_minres_pipe.py)
+    monkeypatch.setenv("HS_MINRES_PIPE", "0")
     hv, H, diag, A, sigma = _sys(L, seed=7)
     b = to_dev(inputs.gaussian(A.shape[0], 2))
     with hs.Chain(L, hv, sigma=sigma) as c:
         x1, i1 = c.minres(b, tol=1e-10)
+    assert i1["form"] == hs.FORM_SMEM
     import subprocess, sys, os
     code = f"""
 import sys; sys.path.insert(0, {os.getcwd()!r})
