@@ -150,10 +150,12 @@ def parse():
                     help="skip the iteration-model solves (value then null)")
     ap.add_argument("--static-budget", action="store_true", dest="static_budget")
     ap.add_argument("--detail", default=None, help="write per-step records to this JSON file")
-    ap.add_argument("--only", choices=["hv", "minres", "forms"], default=None,
+    ap.add_argument("--only", choices=["hv", "minres", "forms", "smem"], default=None,
                     help="profiling cases: only the H x timing at --L; one capped MINRES "
-                         "solve (FP32 + refinement) of --minres-iters iterations at --L; or the "
-                         "products and MINRES iterations of every row form at L = 24, 26, 28")
+                         "solve (FP32 + refinement) of --minres-iters iterations at --L; the "
+                         "products and MINRES iterations of every row form at L = 24, 26, 28; "
+                         "or --minres-iters FP64 and FP32 iterations of the one- and "
+                         "two-reduction shared-memory forms at --L (L <= 20)")
     ap.add_argument("--minres-iters", type=int, default=200, dest="minres_iters")
     return ap.parse_args()
 
@@ -777,6 +779,39 @@ def forms_table(torch, hs, inputs):
     return out
 
 
+def smem_forms(torch, hs, inputs, L, iters):
+    """Microseconds per MINRES iteration (row norm, tolerance 0, `iters`
+    iterations in one launch) of the one-reduction (HS_MINRES_PIPE=1) and the
+    two-reduction (=0) shared-memory forms, FP64 then FP32, on all SMs, CUDA
+    events on the current stream; one launch of each kernel per case."""
+    out = {}
+    saved = os.environ.get("HS_MINRES_PIPE")
+    try:
+        with hs.Chain(L, inputs.disorder(L, L28_H, 0), sigma=0.05) as c:
+            b = torch.randn(c.n, dtype=torch.float64, device="cuda")
+            for name in ("f64", "f32"):
+                for form in ("1", "0"):
+                    os.environ["HS_MINRES_PIPE"] = form
+                    bb = b if name == "f64" else b.float()
+                    run = c.minres if name == "f64" else c.minres_f32
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    x, info = run(bb, tol=0.0, kmax=iters, precond="row", allow_not_converged=True)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    key = f"L={L} {name} {'one' if form == '1' else 'two'}-reduction"
+                    out[key] = {"us_per_iter": e0.elapsed_time(e1) * 1e3 / info["iters"],
+                                "form": info["form"]}
+    finally:
+        if saved is None:
+            os.environ.pop("HS_MINRES_PIPE", None)
+        else:
+            os.environ["HS_MINRES_PIPE"] = saved
+    return out
+
+
 def run_only(args):
     """Single-kernel cases for profiler captures."""
     import torch
@@ -785,6 +820,9 @@ def run_only(args):
     torch.cuda.set_device(0)
     if args.only == "forms":
         print(json.dumps(forms_table(torch, hs, inputs)))
+        return
+    if args.only == "smem":
+        print(json.dumps(smem_forms(torch, hs, inputs, args.L, args.minres_iters)))
         return
     if args.only == "hv":
         rf = hv_roofline(torch, hs, args.L, torch.cuda.current_stream())

@@ -240,61 +240,39 @@ __global__ void __launch_bounds__(HV_THREADS) k_minres_persist(Geo g, const T* _
 // forms (rows_* above).
 
 template <typename T, int PC, int JM, int NT>
-__global__ void __launch_bounds__(NT, 1) k_minres_smem(
-    Geo g, const T* __restrict__ bv, T* qg0, T* qg1, T* xout, MinresState* st, double tol,
-    long long kmax, const double* d_sigma, double* part, GridBar gb, unsigned long long limit,
-    const int* __restrict__ cta_first, int rows_cap, unsigned long long* trace) {
+__global__ void __launch_bounds__(NT, 1) k_minres_smem(SmemJob job0, SmemQueue q0, SmemQueue q1,
+                                                       int ctas0) {
   extern __shared__ __align__(16) char smem[];
   __shared__ MinresState S;
+  __shared__ SmemJob sj;
   __shared__ double sbuf[4];
   __shared__ double s_ib, s_ibp;
   __shared__ int s_ok;
-  LowEntry* low = reinterpret_cast<LowEntry*>(smem);
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(g.low);
-    uint4* dst = reinterpret_cast<uint4*>(low);
-    for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
-  }
-  const int b0 = cta_first[blockIdx.x], nbk = cta_first[blockIdx.x + 1] - b0;
-  uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * g.nlow);
-  {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
-    for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
-  }
-  size_t off = sizeof(LowEntry) * g.nlow + 128 * (size_t)nbk;
-  off = (off + 15) & ~size_t(15);
-  T* QL0 = reinterpret_cast<T*>(smem + off);
-  T* QL1 = QL0 + rows_cap;
-  T* P = QL0 + 2 * rows_cap;
-  T* D0 = QL0 + 3 * rows_cap;
-  T* D1 = QL0 + 4 * rows_cap;
-  T* X = QL0 + 5 * rows_cap;
-  T* MV = QL0 + 6 * rows_cap;        // M_ii
-  T* MI = QL0 + 7 * rows_cap;        // 1 / M_ii
-  T* DG = QL0 + 8 * rows_cap;        // a_ii - sigma (rebuilding it costs ~4 FP64 operations a row)
-  off += 9 * sizeof(T) * (size_t)rows_cap;
-  off = (off + 15) & ~size_t(15);
-  double* stmp = reinterpret_cast<double*>(smem + off);
-  const uint32_t Rbase = __ldg(&g.blocks[b0].R);
-  const double sigma = *d_sigma;
+  const bool second = (int)blockIdx.x >= ctas0;
+  const SmemQueue& q = second ? q1 : q0;
+  const int lb0 = (int)blockIdx.x - (second ? ctas0 : 0);
+  const int G = q.S, grp = lb0 / G, cta = lb0 - grp * G;
+  Slot* slots = reinterpret_cast<Slot*>(q.slots) + (size_t)grp * 2 * G;
+  T* qg0 = reinterpret_cast<T*>(q.w[0]) + (size_t)grp * q.ws_stride;
+  T* qg1 = reinterpret_cast<T*>(q.w[1]) + (size_t)grp * q.ws_stride;
+  const int b0 = q.cta_first[cta], nbk = q.cta_first[cta + 1] - b0;
+  const int rows_cap = q.rows_cap;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  auto each_block = [&](auto&& f) {
-    for (int lb = wid; lb < nbk; lb += NT / 32) {
-      const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
-      f(h, h.R - Rbase);
-    }
-  };
-  const int G = gridDim.x;
+  // layout (the same for every job of the launch): low table, block headers,
+  // 9 row arrays, reduction scratch
+  size_t off_rows = sizeof(LowEntry) * q.nlow + 128 * (size_t)nbk;
+  off_rows = (off_rows + 15) & ~size_t(15);
+  size_t off_tmp = off_rows + 9 * sizeof(T) * (size_t)rows_cap;
+  off_tmp = (off_tmp + 15) & ~size_t(15);
+  double* stmp = reinterpret_cast<double*>(smem + off_tmp);
   unsigned gen = 0;
-  Slot* slots = reinterpret_cast<Slot*>(part);
   auto reduce = [&](T a, T b, double (&tot)[2]) -> bool {
     double c0, c1;
     cta_sum2<T>(a, b, stmp, c0, c1);
     ++gen;
     if (wid == 0) {
       double t[2];
-      const bool okw = slot_reduce_w0(slots, G, gen, c0, c1, t, limit, gb.err);
+      const bool okw = slot_reduce_w0(slots, G, cta, gen, c0, c1, t, q.limit, q.err);
       if (lane == 0) { sbuf[0] = t[0]; sbuf[1] = t[1]; s_ok = okw; }
     }
     __syncthreads();
@@ -302,125 +280,158 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem(
     tot[1] = sbuf[1];
     return s_ok != 0;
   };
-  bool ok;
-  {
-    T acc = T(0), zm = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) {
-        T am;
-        const T m = row_m<T, PC>(low[h.off + r], h, am);
-        const uint32_t i = h.R + r;
-        const uint32_t l = l0 + r;
-        const T b = bv[i];
-        zm += (m == T(0)) ? T(1) : T(0);
-        const T mi = m == T(0) ? T(0) : T(1) / m;
-        const T q = b * mi;
-        MV[l] = m; MI[l] = mi; DG[l] = am;
-        QL1[l] = q; qg1[i] = q;
-        QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
-        acc += q * b;
-      }
-    });
-    double tot[2];
-    ok = reduce(acc, zm, tot);
-    if (ok && threadIdx.x == 0) {
-      init_state(S, tot[0], tot[1], tol, kmax, sigma);
-      s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
-      s_ibp = 1.0;                     // 1 / beta_0
-    }
-    __syncthreads();
-  }
-  long long tk = 0;
-  auto stamp = [&](int ph) {
-    if (trace && blockIdx.x == 0 && threadIdx.x == 0 && tk >= 16 && tk < 48) {
-      unsigned long long t;
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      trace[(tk - 16) * 8 + ph] = t;
-    }
-  };
-  while (ok && S.done != 2) {
-    ++tk;
-    stamp(0);
-    const long long k = S.k;
-    const bool odd = (k & 1) != 0;
-    T* QLc = odd ? QL1 : QL0;          // q_k
-    T* QLp = odd ? QL0 : QL1;          // q_{k-1} -> q_{k+1}
-    const T* qgc = odd ? qg1 : qg0;    // q_k (global, for gathers)
-    T* qgn = odd ? qg0 : qg1;          // q_{k+1}
-    T* DA = odd ? D1 : D0;             // d_{k-2}
-    T* DB = odd ? D0 : D1;             // d_{k-3} -> d_{k-1}
-    const bool doC = S.pending != 0, doMV = S.done == 0;
-    const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
-    T acc = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      if (doC)
-        for (int r = lane; r < h.C; r += 32) {
-          const uint32_t l = l0 + r;
-          const T d = cq * QLp[l] + cd1 * DA[l] + cd2 * DB[l];
-          DB[l] = d;
-          X[l] += tau * d;
-        }
-      if (doMV) {
-        T xi[JM], hx[JM];
-        block_hv_loc<T, JM>(qgc, QLc + l0, DG + l0, low, h, xi, hx);
-#pragma unroll
-        for (int j = 0; j < JM; ++j) {
-          const int r = lane + 32 * j;
-          if (j < h.J && r < h.C) {
-            P[l0 + r] = hx[j];
-            acc += xi[j] * hx[j];
-          }
-        }
-      }
-    });
-    if (!doMV) {
-      __syncthreads();
-      if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
-      __syncthreads();
+  bool ok = true;
+  for (int njob = 0;; ++njob) {
+    // the next job: CTA 0 of the group takes it from the queue and a group
+    // reduction hands the index to the other CTAs
+    int jid = 0;
+    if (q.jobs) {
+      double tot[2];
+      const T v = (cta == 0 && threadIdx.x == 0) ? (T)atomicAdd(q.head, 1) : T(0);
+      if (!(ok = reduce(v, T(0), tot))) break;
+      jid = (int)tot[0];
+      if (jid >= __ldcg(q.head + 1)) break;
+    } else if (njob > 0) {
       break;
     }
-    stamp(1);
-    double tot[2];
-    if (!(ok = reduce(acc, T(0), tot))) break;
-    stamp(2);
-    if (threadIdx.x == 0) {
-      S.pending = 0;
-      S.alpha = tot[0] * s_ib * s_ib;                   // q.p / beta_k^2
-      if (!isfinite(S.alpha)) { S.status = HS_NONFINITE; S.done = 2; }
-    }
+    if (threadIdx.x == 0) sj = q.jobs ? q.jobs[jid] : job0;
     __syncthreads();
-    if (S.done == 2) break;
-    stamp(3);
-    const T c1 = (T)s_ib, c2 = (T)(S.alpha * s_ib), c3 = (T)(S.beta * s_ibp);
-    T acc2 = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) {
-        const uint32_t l = l0 + r;
-        const T q = P[l] * MI[l] * c1 - c2 * QLc[l] - c3 * QLp[l];
-        QLp[l] = q;
-        qgn[h.R + r] = q;
-        acc2 += MV[l] * q * q;
+    const Geo& g = sj.g;
+    const T* __restrict__ bv = reinterpret_cast<const T*>(sj.b);
+    T* xout = reinterpret_cast<T*>(sj.x);
+    const double sigma = sj.sigma;
+    LowEntry* low = reinterpret_cast<LowEntry*>(smem);
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(g.low);
+      uint4* dst = reinterpret_cast<uint4*>(low);
+      for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * q.nlow);
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
+      for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
+    }
+    T* QL0 = reinterpret_cast<T*>(smem + off_rows);
+    T* QL1 = QL0 + rows_cap;
+    T* P = QL0 + 2 * rows_cap;
+    T* D0 = QL0 + 3 * rows_cap;
+    T* D1 = QL0 + 4 * rows_cap;
+    T* X = QL0 + 5 * rows_cap;
+    T* MV = QL0 + 6 * rows_cap;        // M_ii
+    T* MI = QL0 + 7 * rows_cap;        // 1 / M_ii
+    T* DG = QL0 + 8 * rows_cap;        // a_ii - sigma (rebuilding it costs ~4 FP64 operations a row)
+    const uint32_t Rbase = nbk > 0 ? __ldg(&g.blocks[b0].R) : 0u;
+    __syncthreads();
+    auto each_block = [&](auto&& f) {
+      for (int lb = wid; lb < nbk; lb += NT / 32) {
+        const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+        f(h, h.R - Rbase);
       }
-    });
-    stamp(4);
-    if (!(ok = reduce(acc2, T(0), tot))) break;
-    stamp(5);
-    if (threadIdx.x == 0) {
-      double ib = s_ib;
-      givens_fast(S, tot[0], ib);
-      s_ibp = s_ib;
-      s_ib = ib;
+    };
+    {
+      T acc = T(0), zm = T(0);
+      each_block([&](const Hdr& h, uint32_t l0) {
+        for (int r = lane; r < h.C; r += 32) {
+          T am;
+          const T m = row_m<T, PC>(low[h.off + r], h, am);
+          const uint32_t i = h.R + r;
+          const uint32_t l = l0 + r;
+          const T b = bv[i];
+          zm += (m == T(0)) ? T(1) : T(0);
+          const T mi = m == T(0) ? T(0) : T(1) / m;
+          const T qv = b * mi;
+          MV[l] = m; MI[l] = mi; DG[l] = am;
+          QL1[l] = qv; qg1[i] = qv;
+          QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
+          acc += qv * b;
+        }
+      });
+      double tot[2];
+      ok = reduce(acc, zm, tot);
+      if (ok && threadIdx.x == 0) {
+        init_state(S, tot[0], tot[1], sj.tol, sj.kmax, sigma);
+        s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
+        s_ibp = 1.0;                     // 1 / beta_0
+      }
+      __syncthreads();
+    }
+    while (ok && S.done != 2) {
+      const long long k = S.k;
+      const bool odd = (k & 1) != 0;
+      T* QLc = odd ? QL1 : QL0;          // q_k
+      T* QLp = odd ? QL0 : QL1;          // q_{k-1} -> q_{k+1}
+      const T* qgc = odd ? qg1 : qg0;    // q_k (global, for gathers)
+      T* qgn = odd ? qg0 : qg1;          // q_{k+1}
+      T* DA = odd ? D1 : D0;             // d_{k-2}
+      T* DB = odd ? D0 : D1;             // d_{k-3} -> d_{k-1}
+      const bool doC = S.pending != 0, doMV = S.done == 0;
+      const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
+      T acc = T(0);
+      each_block([&](const Hdr& h, uint32_t l0) {
+        if (doC)
+          for (int r = lane; r < h.C; r += 32) {
+            const uint32_t l = l0 + r;
+            const T d = cq * QLp[l] + cd1 * DA[l] + cd2 * DB[l];
+            DB[l] = d;
+            X[l] += tau * d;
+          }
+        if (doMV) {
+          T xi[JM], hx[JM];
+          block_hv_loc<T, JM>(qgc, QLc + l0, DG + l0, low, h, xi, hx);
+#pragma unroll
+          for (int j = 0; j < JM; ++j) {
+            const int r = lane + 32 * j;
+            if (j < h.J && r < h.C) {
+              P[l0 + r] = hx[j];
+              acc += xi[j] * hx[j];
+            }
+          }
+        }
+      });
+      if (!doMV) {
+        __syncthreads();
+        if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
+        __syncthreads();
+        break;
+      }
+      double tot[2];
+      if (!(ok = reduce(acc, T(0), tot))) break;
+      if (threadIdx.x == 0) {
+        S.pending = 0;
+        S.alpha = tot[0] * s_ib * s_ib;                   // q.p / beta_k^2
+        if (!isfinite(S.alpha)) { S.status = HS_NONFINITE; S.done = 2; }
+      }
+      __syncthreads();
+      if (S.done == 2) break;
+      const T c1 = (T)s_ib, c2 = (T)(S.alpha * s_ib), c3 = (T)(S.beta * s_ibp);
+      T acc2 = T(0);
+      each_block([&](const Hdr& h, uint32_t l0) {
+        for (int r = lane; r < h.C; r += 32) {
+          const uint32_t l = l0 + r;
+          const T qv = P[l] * MI[l] * c1 - c2 * QLc[l] - c3 * QLp[l];
+          QLp[l] = qv;
+          qgn[h.R + r] = qv;
+          acc2 += MV[l] * qv * qv;
+        }
+      });
+      if (!(ok = reduce(acc2, T(0), tot))) break;
+      if (threadIdx.x == 0) {
+        double ib = s_ib;
+        givens_fast(S, tot[0], ib);
+        s_ibp = s_ib;
+        s_ib = ib;
+      }
+      __syncthreads();
     }
     __syncthreads();
-    stamp(6);
-  }
-  __syncthreads();
-  each_block([&](const Hdr& h, uint32_t l0) {
-    for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
-  });
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
-    *st = S;
+    each_block([&](const Hdr& h, uint32_t l0) {
+      for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
+    });
+    if (cta == 0 && threadIdx.x == 0) {
+      if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
+      *sj.st = S;
+    }
+    if (!ok) break;
   }
 }
 
@@ -629,94 +640,111 @@ hs_status smr_plan(hs_handle* hd, int G, int** d_first, int* rows_cap, int* hdr_
   return HS_OK;
 }
 
-// Shared-memory-resident solve; HS_CUDA without a message when it does not fit.
+// Launch of the two-reduction kernel for one or two queues; HS_CUDA without a
+// message when it does not fit in shared memory or the cooperative launch is
+// refused.
 template <typename T, int PC, int JM, int NT>
-static hs_status solve_smem_v(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
-                              long long kmax) {
-  const int bud = hd->sm_budget.load(std::memory_order_relaxed);
-  const int G = std::max(1, std::min(hd->num_sms, bud > 0 ? bud : hd->num_sms));
-  int* first = nullptr;
-  int rows_cap = 0, hdr_cap = 0;
-  hs_status st = smr_plan(hd, G, &first, &rows_cap, &hdr_cap);
-  if (st != HS_OK) return st;
+static hs_status launch2_t(int device, cudaStream_t s, const SmemJob& job0,
+                           const SmemQueue (&q)[2], const int (&ng)[2], const int (&hc)[2]) {
   int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, hd->device);
-  const size_t sm = smr_bytes<T>((int)hd->low.size(), hdr_cap, rows_cap, NT);
-  const size_t static_sm = sizeof(MinresState) + 8 * 8 + 64;
-  if (sm + static_sm > (size_t)optin) return HS_CUDA;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  size_t sm = smr_bytes<T>(q[0].nlow, hc[0], q[0].rows_cap, NT);
+  if (ng[1] > 0) sm = std::max(sm, smr_bytes<T>(q[1].nlow, hc[1], q[1].rows_cap, NT));
+  if (sm + SMEM_STATIC_BYTES > (size_t)optin) return HS_CUDA;
   if (cudaFuncSetAttribute(k_minres_smem<T, PC, JM, NT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
     cudaGetLastError();
     return HS_CUDA;
   }
-  Geo g = hd->geo();
-  GridBar gb{hd->d_counter + 8, hd->d_counter + 9, reinterpret_cast<int*>(hd->d_counter + 10)};
-  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_counter + 8, 0, 3 * sizeof(unsigned), hd->stream));
-  // generation slots start from zero for every solve (a stale generation left
-  // by a previous solve must never read as an arrival)
-  if (G > 256) return HS_CUDA;
-  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_partial, 0, 2 * sizeof(Slot) * G, hd->stream));
-  double* part = hd->d_partial;
-  const double* ds = hd->d_sigma;
-  MinresState* stp = hd->d_state;
-  unsigned long long limit = 1ull << 22;
-  if (const char* e = getenv("HS_BARRIER_LIMIT")) limit = strtoull(e, nullptr, 10);
-  T* q0 = (T*)v.q0;
-  T* q1 = (T*)v.q1;
-  T* xo = (T*)v.x;
-  unsigned long long* trace = nullptr;
-  const bool want_trace = getenv("HS_TRACE") != nullptr;
-  if (want_trace) {
-    HS_CUDA_TRY(hd, cudaMalloc(&trace, 32 * 8 * sizeof(unsigned long long)));
-    HS_CUDA_TRY(hd, cudaMemsetAsync(trace, 0, 32 * 8 * sizeof(unsigned long long), hd->stream));
-  }
-  void* args[] = {&g, (void*)&b, &q0, &q1, &xo, &stp, &tol, &kmax, (void*)&ds, &part, &gb, &limit,
-                  &first, &rows_cap, &trace};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_minres_smem<T, PC, JM, NT>, dim3(G),
-                                              dim3(NT), args, sm, hd->stream);
+  SmemJob j = job0;
+  SmemQueue q0 = q[0], q1 = ng[1] > 0 ? q[1] : q[0];
+  int ctas0 = ng[0] * q[0].S;
+  void* args[] = {&j, &q0, &q1, &ctas0};
+  const int grid = ctas0 + (ng[1] > 0 ? ng[1] * q[1].S : 0);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_minres_smem<T, PC, JM, NT>,
+                                                    dim3(grid), dim3(NT), args, sm, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return HS_CUDA;
   }
   count_launches(1);
-  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
-                                  cudaMemcpyDeviceToHost, hd->stream));
-  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
-  if (want_trace) {
-    std::vector<unsigned long long> t(32 * 8);
-    cudaMemcpy(t.data(), trace, t.size() * 8, cudaMemcpyDeviceToHost);
-    cudaFree(trace);
-    double acc[7] = {0};
-    int cnt = 0;
-    for (int it = 0; it + 1 < 32; ++it) {
-      const unsigned long long* a = &t[it * 8];
-      const unsigned long long* nx = &t[(it + 1) * 8];
-      if (!a[0] || !nx[0] || !a[6]) continue;
-      for (int ph = 0; ph < 6; ++ph) acc[ph] += (double)(a[ph + 1] - a[ph]);
-      acc[6] += (double)(nx[0] - a[6]);
-      ++cnt;
-    }
-    if (cnt)
-      fprintf(stderr,
-              "[hs trace] G=%d ns/iter: rowsA %.0f redA %.0f scalA %.0f rowsB %.0f redB %.0f "
-              "scalB %.0f loop %.0f total %.0f\n",
-              (int)dim3(G).x, acc[0] / cnt, acc[1] / cnt, acc[2] / cnt, acc[3] / cnt, acc[4] / cnt,
-              acc[5] / cnt, acc[6] / cnt,
-              (acc[0] + acc[1] + acc[2] + acc[3] + acc[4] + acc[5] + acc[6]) / cnt);
-  }
   return HS_OK;
 }
 
-// Blocks of at most 96 rows (k <= 8) take 3 rows per lane and 1024 threads;
-// larger blocks 8 rows per lane and 512 threads.
+// Blocks of at most 96 rows (k <= 8) take 3 rows per lane and 1024 threads
+// (FP32) or 512 (FP64 rows need more than the 64 registers a 1024-thread CTA
+// allows); larger blocks 8 rows per lane and 512 threads.
+template <typename T, int PC>
+static hs_status launch2_pc(int k, int device, cudaStream_t s, const SmemJob& job0,
+                            const SmemQueue (&q)[2], const int (&ng)[2], const int (&hc)[2]) {
+  if (k <= 8) {
+    if constexpr (sizeof(T) == 8) return launch2_t<T, PC, 3, 512>(device, s, job0, q, ng, hc);
+    else return launch2_t<T, PC, 3, 1024>(device, s, job0, q, ng, hc);
+  }
+  return launch2_t<T, PC, JMAX, 512>(device, s, job0, q, ng, hc);
+}
+
+hs_status launch_smem2(hs_dtype dt, int pc, int k, int device, cudaStream_t s,
+                       const SmemJob& job0, const SmemQueue (&q)[2], const int (&ng)[2],
+                       const int (&hc)[2]) {
+  if (dt == HS_F64)
+    return pc == 0 ? launch2_pc<double, 0>(k, device, s, job0, q, ng, hc)
+         : pc == 1 ? launch2_pc<double, 1>(k, device, s, job0, q, ng, hc)
+                   : launch2_pc<double, 2>(k, device, s, job0, q, ng, hc);
+  return pc == 0 ? launch2_pc<float, 0>(k, device, s, job0, q, ng, hc)
+       : pc == 1 ? launch2_pc<float, 1>(k, device, s, job0, q, ng, hc)
+                 : launch2_pc<float, 2>(k, device, s, job0, q, ng, hc);
+}
+
+// One solve in a shared-memory form (one job, one group of G CTAs): the queue
+// of the handle's workspace. one = the one-reduction kernel (minres_pipe.cu).
+// HS_CUDA without a message when the form does not apply.
+hs_status solve_smem_job(hs_handle* hd, const void* b, const MinresVecs& v, hs_dtype dt, int pc,
+                         double tol, long long kmax, bool one) {
+  const int bud = hd->sm_budget.load(std::memory_order_relaxed);
+  const int G = std::max(1, std::min(hd->num_sms, bud > 0 ? bud : hd->num_sms));
+  if (G > 256) return HS_CUDA;
+  int* first = nullptr;
+  int rows_cap = 0, hdr_cap = 0;
+  hs_status st = smr_plan(hd, G, &first, &rows_cap, &hdr_cap);
+  if (st != HS_OK) return st;
+  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_counter + 10, 0, sizeof(unsigned), hd->stream));
+  // generation slots start from zero for every solve (a stale generation left
+  // by a previous solve must never read as an arrival)
+  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_partial, 0, 2 * sizeof(SlotN) * G, hd->stream));
+  unsigned long long limit = 1ull << 22;
+  if (const char* e = getenv("HS_BARRIER_LIMIT")) limit = strtoull(e, nullptr, 10);
+  SmemJob job{hd->geo(), b, v.x, hd->d_state, hd->sigma, tol, kmax};
+  SmemQueue q{};
+  q.jobs = nullptr;
+  q.head = nullptr;
+  q.S = G;
+  q.nlow = (int)hd->low.size();
+  q.slots = hd->d_partial;
+  q.err = reinterpret_cast<int*>(hd->d_counter + 10);
+  q.limit = limit;
+  q.cta_first = first;
+  q.rows_cap = rows_cap;
+  q.w[0] = v.q0; q.w[1] = v.q1; q.w[2] = v.p;
+  q.ws_stride = 0;
+  const SmemQueue qs[2] = {q, q};
+  const int ng[2] = {1, 0}, hc[2] = {hdr_cap, 0};
+  st = one ? launch_smem1(dt, pc, hd->k, hd->device, hd->stream, job, qs, ng, hc,
+                          pipe_replace_period())
+           : launch_smem2(dt, pc, hd->k, hd->device, hd->stream, job, qs, ng, hc);
+  if (st != HS_OK) return st;
+  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
+                                  cudaMemcpyDeviceToHost, hd->stream));
+  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
+  const MinresState& S = *hd->h_state;
+  if (one && S.status == HS_BREAKDOWN && S.pad == PIPE_EXPANSION) return HS_CUDA;
+  return HS_OK;
+}
+
 template <typename T, int PC>
 static hs_status solve_smem(hs_handle* hd, const T* b, const MinresVecs& v, double tol,
                             long long kmax) {
-  // FP64 rows need more than the 64 registers a 1024-thread CTA allows
-  if (hd->k <= 8)
-    return sizeof(T) == 8 ? solve_smem_v<T, PC, 3, 512>(hd, b, v, tol, kmax)
-                          : solve_smem_v<T, PC, 3, 1024>(hd, b, v, tol, kmax);
-  return solve_smem_v<T, PC, JMAX, 512>(hd, b, v, tol, kmax);
+  return solve_smem_job(hd, b, v, sizeof(T) == 8 ? HS_F64 : HS_F32, PC, tol, kmax, false);
 }
 
 template <typename T, int PC>
@@ -866,7 +894,7 @@ static hs_status solve_pc(hs_handle* hd, const T* b, T* x, double tol, long long
   const int sbc = sb_choice(hd);
   if (sbc == 2 && (st = try_sb<T, PC>(hd, b, v, tol, kmax)) != HS_CUDA) form = HS_FORM_SUPERBLOCK;
   if (st == HS_CUDA && !force_graph() && !force_global() && pipe_choice(hd, sizeof(T) == 8, PC) &&
-      (st = minres_solve_pipe(hd, b, v, sizeof(T) == 8 ? HS_F64 : HS_F32, PC, tol, kmax)) !=
+      (st = solve_smem_job(hd, b, v, sizeof(T) == 8 ? HS_F64 : HS_F32, PC, tol, kmax, true)) !=
           HS_CUDA)
     form = HS_FORM_SMEM1;
   if (st == HS_CUDA && !force_graph() && !force_global() &&

@@ -29,6 +29,7 @@
 // extra barrier). Where the expansion cancels to rounding level (beta_{k+1}^2
 // below EXPANSION_FLOOR of its terms) the solve ends with HS_BREAKDOWN and
 // pad = PIPE_EXPANSION, and the caller solves again with the two-reduction form.
+#include <algorithm>
 #include <cstdlib>
 
 #include "minres_smem.cuh"
@@ -38,7 +39,6 @@ namespace hs {
 namespace {
 
 constexpr int PIPE_NV = 5;           // S1..S5 (S6 is carried)
-constexpr int PIPE_EXPANSION = 1;    // MinresState.pad: the expansion was not trusted
 
 // Smallest beta_{k+1}^2 / mag (mag: the sum of the expansion's terms in
 // magnitude) that the expansion is trusted with: its relative error is about
@@ -59,32 +59,38 @@ size_t smr1_bytes(int nlow, int hdr_cap, int rows_cap, int nt) {
 }
 
 template <typename T, int PC, int JM, int NT>
-__global__ void __launch_bounds__(NT, 1) k_minres_smem1(
-    Geo g, const T* __restrict__ bv, T* vg0, T* vg1, T* qg, T* xout, MinresState* st, double tol,
-    long long kmax, int rperiod, const double* d_sigma, SlotN* slots, int* err,
-    unsigned long long limit, const int* __restrict__ cta_first, int rows_cap) {
+__global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue q0, SmemQueue q1,
+                                                        int ctas0, int rperiod) {
   extern __shared__ __align__(16) char smem[];
   __shared__ MinresState S;
+  __shared__ SmemJob sj;
   __shared__ double s_sum[PIPE_NV + 1];   // S1..S5 of the current step, S6
   __shared__ double s_cta[PIPE_NV];
   __shared__ double s_c[3];               // 1/beta_k, a, c of the vector update
   __shared__ double s_ib, s_ibp;          // 1/beta_k, 1/beta_{k-1}
   __shared__ int s_ok;
+  const bool second = (int)blockIdx.x >= ctas0;
+  const SmemQueue& q = second ? q1 : q0;
+  const int lb0 = (int)blockIdx.x - (second ? ctas0 : 0);
+  const int G = q.S, grp = lb0 / G, cta = lb0 - grp * G;
+  SlotN* slots = reinterpret_cast<SlotN*>(q.slots) + (size_t)grp * 2 * G;
+  T* vg0 = reinterpret_cast<T*>(q.w[0]) + (size_t)grp * q.ws_stride;
+  T* vg1 = reinterpret_cast<T*>(q.w[1]) + (size_t)grp * q.ws_stride;
+  T* qg = reinterpret_cast<T*>(q.w[2]) + (size_t)grp * q.ws_stride;
+  const int b0 = q.cta_first[cta], nbk = q.cta_first[cta + 1] - b0;
+  const int rows_cap = q.rows_cap;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nact = min(nbk, NT / 32);         // warps that own blocks
+  // layout (the same for every job of the launch): low table, block headers,
+  // 11 row arrays, reduction staging
+  size_t off_rows = sizeof(LowEntry) * q.nlow + 128 * (size_t)nbk;
+  off_rows = (off_rows + 15) & ~size_t(15);
+  size_t off_tmp = off_rows + 11 * sizeof(T) * (size_t)rows_cap;
+  off_tmp = (off_tmp + 15) & ~size_t(15);
+  double* stmp = reinterpret_cast<double*>(smem + off_tmp);
   LowEntry* low = reinterpret_cast<LowEntry*>(smem);
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(g.low);
-    uint4* dst = reinterpret_cast<uint4*>(low);
-    for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
-  }
-  const int b0 = cta_first[blockIdx.x], nbk = cta_first[blockIdx.x + 1] - b0;
-  uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * g.nlow);
-  {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
-    for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
-  }
-  size_t off = sizeof(LowEntry) * g.nlow + 128 * (size_t)nbk;
-  off = (off + 15) & ~size_t(15);
-  T* Q0 = reinterpret_cast<T*>(smem + off);   // q_j in Q[j & 1]
+  uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * q.nlow);
+  T* Q0 = reinterpret_cast<T*>(smem + off_rows);   // q_j in Q[j & 1]
   T* Q1 = Q0 + rows_cap;
   T* P0 = Q0 + 2 * rows_cap;                  // p_j in P[j & 1]
   T* P1 = Q0 + 3 * rows_cap;
@@ -95,28 +101,13 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(
   T* MV = Q0 + 8 * rows_cap;                  // M_ii
   T* MI = Q0 + 9 * rows_cap;                  // 1 / M_ii
   T* DG = Q0 + 10 * rows_cap;                 // a_ii - sigma
-  off += 11 * sizeof(T) * (size_t)rows_cap;
-  off = (off + 15) & ~size_t(15);
-  double* stmp = reinterpret_cast<double*>(smem + off);
-  const uint32_t Rbase = __ldg(&g.blocks[b0].R);
-  const double sigma = *d_sigma;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nact = min(nbk, NT / 32);         // warps that own blocks
-  __syncthreads();
-  auto each_block = [&](auto&& f) {
-    for (int lb = wid; lb < nbk; lb += NT / 32) {
-      const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
-      f(h, h.R - Rbase);
-    }
-  };
-  const int G = gridDim.x;
   unsigned gen = 0;
   auto reduce = [&](const T (&a)[PIPE_NV]) -> bool {
     cta_sumN<T, PIPE_NV>(a, nact, stmp, s_cta);
     ++gen;
     if (wid == 0) {
       double t[PIPE_NV];
-      const bool okw = slot_reduceN_w0<PIPE_NV>(slots, G, gen, s_cta, t, limit, err);
+      const bool okw = slot_reduceN_w0<PIPE_NV>(slots, G, cta, gen, s_cta, t, q.limit, q.err);
       if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < PIPE_NV; ++j) s_sum[j] = t[j];
@@ -126,179 +117,236 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(
     __syncthreads();
     return s_ok != 0;
   };
-  bool ok;
-  // q_1 = M^-1 b (x_0 = 0), q_0 = p_0 = 0, d_0 = d_{-1} = 0; q_1 is published
-  // for the first product
-  {
-    T a[PIPE_NV] = {};
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) {
-        T am;
-        const T m = row_m<T, PC>(low[h.off + r], h, am);
-        const uint32_t i = h.R + r;
-        const uint32_t l = l0 + r;
-        const T b = bv[i];
-        a[1] += (m == T(0)) ? T(1) : T(0);
-        const T mi = m == T(0) ? T(0) : T(1) / m;
-        const T q = b * mi;
-        MV[l] = m; MI[l] = mi; DG[l] = am;
-        Q1[l] = q; qg[i] = q;
-        Q0[l] = T(0); P0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
-        a[0] += q * b;
-      }
-    });
-    ok = reduce(a);
-    if (ok && threadIdx.x == 0) {
-      init_state(S, s_sum[0], s_sum[1], tol, kmax, sigma);
-      s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
-      s_ibp = 1.0;                             // 1 / beta_0
-    }
+  // a reduction of one value held by thread 0 (the others contribute 0)
+  auto reduce_one = [&](double v) -> bool {
     __syncthreads();
-  }
-  // p_1 = (H - sigma) q_1, v_1 and the sums of step 1 (S3 = S5 = S6 = 0)
-  if (ok && S.done == 0) {
-    T a[PIPE_NV] = {};
-    each_block([&](const Hdr& h, uint32_t l0) {
-      T xi[JM], hx[JM];
-      block_hv_loc<T, JM>(qg, Q1 + l0, DG + l0, low, h, xi, hx);
+    if (threadIdx.x < PIPE_NV) s_cta[threadIdx.x] = threadIdx.x == 0 ? v : 0.0;
+    __syncthreads();
+    ++gen;
+    if (wid == 0) {
+      double t[PIPE_NV];
+      const bool okw = slot_reduceN_w0<PIPE_NV>(slots, G, cta, gen, s_cta, t, q.limit, q.err);
+      if (lane == 0) {
 #pragma unroll
-      for (int j = 0; j < JM; ++j) {
-        const int r = lane + 32 * j;
-        if (j < h.J && r < h.C) {
-          const uint32_t l = l0 + r;
-          const T p = hx[j];
-          const T v = MI[l] * p;
-          P1[l] = p; VL[l] = v; vg1[h.R + r] = v;
-          a[0] += xi[j] * p;
-          a[1] += p * v;
-          a[3] += MV[l] * xi[j] * xi[j];
-        }
-      }
-    });
-    ok = reduce(a);
-    if (threadIdx.x == 0) s_sum[PIPE_NV] = 0.0;
-    __syncthreads();
-  }
-  while (ok && S.done == 0) {
-    // scalars of step k
-    if (threadIdx.x == 0) {
-      const double bk = S.beta, ib = s_ib;
-      const double S1 = s_sum[0], S2 = s_sum[1], S3 = s_sum[2], S4 = s_sum[3], S5 = s_sum[4];
-      const double S6 = s_sum[5];
-      const double alpha = S1 * ib * ib;                         // alpha_k
-      const double a = alpha * ib, c = bk * s_ibp;
-      const double b2 = S2 * ib * ib + a * a * S4 + c * c * S6 - 2.0 * a * S1 * ib -
-                        2.0 * c * S3 * ib + 2.0 * a * c * S5;   // beta_{k+1}^2
-      // the terms' magnitude: b2 carries a rounding error of about
-      // u mag, with u the unit roundoff of the vectors
-      const double mag = S2 * ib * ib + a * a * S4 + c * c * S6 + fabs(2.0 * a * S1 * ib) +
-                         fabs(2.0 * c * S3 * ib) + fabs(2.0 * a * c * S5);
-      s_c[0] = ib; s_c[1] = a; s_c[2] = c;
-      s_sum[5] = S4;
-      S.alpha = alpha;
-      if (!isfinite(alpha) || !isfinite(b2)) {
-        S.status = HS_NONFINITE; S.done = 2; S.pending = 0;
-      } else if (!(b2 > EXPANSION_FLOOR<T> * mag)) {
-        S.status = HS_BREAKDOWN; S.pad = PIPE_EXPANSION; S.done = 2; S.pending = 0;
-      } else {
-        double ibn = ib;
-        givens_fast(S, b2, ibn);
-        s_ibp = ib;
-        s_ib = ibn;
+        for (int j = 0; j < PIPE_NV; ++j) s_sum[j] = t[j];
+        s_ok = okw;
       }
     }
     __syncthreads();
-    if (S.done == 2) break;
-    const long long kk = S.k - 1;               // the step just rotated
-    const bool doMV = S.done == 0;
-    const bool repl = doMV && rperiod > 0 && (kk % rperiod) == 0;
-    const bool odd = (kk & 1) != 0;
-    const T* Qk = odd ? Q1 : Q0;                // q_k
-    T* Qm = odd ? Q0 : Q1;                      // q_{k-1} -> q_{k+1}
-    const T* Pk = odd ? P1 : P0;                // p_k
-    T* Pm = odd ? P0 : P1;                      // p_{k-1} -> p_{k+1}
-    const T* Dm = odd ? D0 : D1;                // d_{k-1}
-    T* Dk = odd ? D1 : D0;                      // d_{k-2} -> d_k
-    const T* vgk = odd ? vg1 : vg0;             // v_k
-    T* vgn = odd ? vg0 : vg1;                   // v_{k+1}
-    const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
-    const T c1 = (T)s_c[0], c2 = (T)s_c[1], c3 = (T)s_c[2];
-    T a[PIPE_NV] = {};
-    each_block([&](const Hdr& h, uint32_t l0) {
-      // d_k = (q_k / beta_k - delta_k d_{k-1} - eps_k d_{k-2}) / gamma_k, x_k
-      for (int r = lane; r < h.C; r += 32) {
-        const uint32_t l = l0 + r;
-        const T d = cq * Qk[l] + cd1 * Dm[l] + cd2 * Dk[l];
-        Dk[l] = d;
-        X[l] += tau * d;
-      }
-      if (!doMV) return;
-      if (repl) {
-        for (int r = lane; r < h.C; r += 32) {
-          const uint32_t l = l0 + r;
-          const T q = c1 * VL[l] - c2 * Qk[l] - c3 * Qm[l];
-          Qm[l] = q;
-          qg[h.R + r] = q;
-        }
-        return;
-      }
-      T xi[JM], hx[JM];
-      block_hv_loc<T, JM>(vgk, VL + l0, DG + l0, low, h, xi, hx);   // xi = v_k
-      __syncwarp();                             // the block's reads of VL are done
-#pragma unroll
-      for (int j = 0; j < JM; ++j) {
-        const int r = lane + 32 * j;
-        if (j < h.J && r < h.C) {
-          const uint32_t l = l0 + r;
-          const T qo = Qk[l];
-          const T q = c1 * xi[j] - c2 * qo - c3 * Qm[l];
-          const T p = c1 * hx[j] - c2 * Pk[l] - c3 * Pm[l];
-          const T v = MI[l] * p;
-          Qm[l] = q; Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
-          const T mq = MV[l] * q;
-          a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
-        }
-      }
-    });
-    if (!doMV) {                                // the last d/x update only
-      __syncthreads();
-      if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
-      __syncthreads();
+    return s_ok != 0;
+  };
+  bool ok = true;
+  for (int njob = 0;; ++njob) {
+    // the next job: CTA 0 of the group takes it from the queue and a group
+    // reduction hands the index to the other CTAs (all warps take part)
+    int jid = 0;
+    if (q.jobs) {
+      if (!(ok = reduce_one(cta == 0 && threadIdx.x == 0 ? (double)atomicAdd(q.head, 1) : 0.0)))
+        break;
+      jid = (int)s_sum[0];
+      if (jid >= __ldcg(q.head + 1)) break;
+    } else if (njob > 0) {
       break;
     }
-    if (repl) {
-      // publish q_{k+1}, then p_{k+1} = (H - sigma) q_{k+1}
-      if (!(ok = reduce(a))) break;
+    if (threadIdx.x == 0) sj = q.jobs ? q.jobs[jid] : job0;
+    __syncthreads();
+    const Geo& g = sj.g;
+    const T* __restrict__ bv = reinterpret_cast<const T*>(sj.b);
+    T* xout = reinterpret_cast<T*>(sj.x);
+    const double sigma = sj.sigma;
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(g.low);
+      uint4* dst = reinterpret_cast<uint4*>(low);
+      for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
+      for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
+    }
+    const uint32_t Rbase = nbk > 0 ? __ldg(&g.blocks[b0].R) : 0u;
+    __syncthreads();
+    auto each_block = [&](auto&& f) {
+      for (int lb = wid; lb < nbk; lb += NT / 32) {
+        const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+        f(h, h.R - Rbase);
+      }
+    };
+    // q_1 = M^-1 b (x_0 = 0), q_0 = p_0 = 0, d_0 = d_{-1} = 0; q_1 is published
+    // for the first product
+    {
+      T a[PIPE_NV] = {};
+      each_block([&](const Hdr& h, uint32_t l0) {
+        for (int r = lane; r < h.C; r += 32) {
+          T am;
+          const T m = row_m<T, PC>(low[h.off + r], h, am);
+          const uint32_t i = h.R + r;
+          const uint32_t l = l0 + r;
+          const T b = bv[i];
+          a[1] += (m == T(0)) ? T(1) : T(0);
+          const T mi = m == T(0) ? T(0) : T(1) / m;
+          const T q = b * mi;
+          MV[l] = m; MI[l] = mi; DG[l] = am;
+          Q1[l] = q; qg[i] = q;
+          Q0[l] = T(0); P0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
+          a[0] += q * b;
+        }
+      });
+      ok = reduce(a);
+      if (ok && threadIdx.x == 0) {
+        init_state(S, s_sum[0], s_sum[1], sj.tol, sj.kmax, sigma);
+        s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
+        s_ibp = 1.0;                             // 1 / beta_0
+      }
+      __syncthreads();
+    }
+    // p_1 = (H - sigma) q_1, v_1 and the sums of step 1 (S3 = S5 = S6 = 0)
+    if (ok && S.done == 0) {
+      T a[PIPE_NV] = {};
       each_block([&](const Hdr& h, uint32_t l0) {
         T xi[JM], hx[JM];
-        block_hv_loc<T, JM>(qg, Qm + l0, DG + l0, low, h, xi, hx);  // xi = q_{k+1}
-#pragma unroll
+        block_hv_loc<T, JM>(qg, Q1 + l0, DG + l0, low, h, xi, hx);
+  #pragma unroll
+        for (int j = 0; j < JM; ++j) {
+          const int r = lane + 32 * j;
+          if (j < h.J && r < h.C) {
+            const uint32_t l = l0 + r;
+            const T p = hx[j];
+            const T v = MI[l] * p;
+            P1[l] = p; VL[l] = v; vg1[h.R + r] = v;
+            a[0] += xi[j] * p;
+            a[1] += p * v;
+            a[3] += MV[l] * xi[j] * xi[j];
+          }
+        }
+      });
+      ok = reduce(a);
+      if (threadIdx.x == 0) s_sum[PIPE_NV] = 0.0;
+      __syncthreads();
+    }
+    while (ok && S.done == 0) {
+      // scalars of step k
+      if (threadIdx.x == 0) {
+        const double bk = S.beta, ib = s_ib;
+        const double S1 = s_sum[0], S2 = s_sum[1], S3 = s_sum[2], S4 = s_sum[3], S5 = s_sum[4];
+        const double S6 = s_sum[5];
+        const double alpha = S1 * ib * ib;                         // alpha_k
+        const double a = alpha * ib, c = bk * s_ibp;
+        const double b2 = S2 * ib * ib + a * a * S4 + c * c * S6 - 2.0 * a * S1 * ib -
+                          2.0 * c * S3 * ib + 2.0 * a * c * S5;   // beta_{k+1}^2
+        // the terms' magnitude: b2 carries a rounding error of about
+        // u mag, with u the unit roundoff of the vectors
+        const double mag = S2 * ib * ib + a * a * S4 + c * c * S6 + fabs(2.0 * a * S1 * ib) +
+                           fabs(2.0 * c * S3 * ib) + fabs(2.0 * a * c * S5);
+        s_c[0] = ib; s_c[1] = a; s_c[2] = c;
+        s_sum[5] = S4;
+        S.alpha = alpha;
+        if (!isfinite(alpha) || !isfinite(b2)) {
+          S.status = HS_NONFINITE; S.done = 2; S.pending = 0;
+        } else if (!(b2 > EXPANSION_FLOOR<T> * mag)) {
+          S.status = HS_BREAKDOWN; S.pad = PIPE_EXPANSION; S.done = 2; S.pending = 0;
+        } else {
+          double ibn = ib;
+          givens_fast(S, b2, ibn);
+          s_ibp = ib;
+          s_ib = ibn;
+        }
+      }
+      __syncthreads();
+      if (S.done == 2) break;
+      const long long kk = S.k - 1;               // the step just rotated
+      const bool doMV = S.done == 0;
+      const bool repl = doMV && rperiod > 0 && (kk % rperiod) == 0;
+      const bool odd = (kk & 1) != 0;
+      const T* Qk = odd ? Q1 : Q0;                // q_k
+      T* Qm = odd ? Q0 : Q1;                      // q_{k-1} -> q_{k+1}
+      const T* Pk = odd ? P1 : P0;                // p_k
+      T* Pm = odd ? P0 : P1;                      // p_{k-1} -> p_{k+1}
+      const T* Dm = odd ? D0 : D1;                // d_{k-1}
+      T* Dk = odd ? D1 : D0;                      // d_{k-2} -> d_k
+      const T* vgk = odd ? vg1 : vg0;             // v_k
+      T* vgn = odd ? vg0 : vg1;                   // v_{k+1}
+      const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
+      const T c1 = (T)s_c[0], c2 = (T)s_c[1], c3 = (T)s_c[2];
+      T a[PIPE_NV] = {};
+      each_block([&](const Hdr& h, uint32_t l0) {
+        // d_k = (q_k / beta_k - delta_k d_{k-1} - eps_k d_{k-2}) / gamma_k, x_k
+        for (int r = lane; r < h.C; r += 32) {
+          const uint32_t l = l0 + r;
+          const T d = cq * Qk[l] + cd1 * Dm[l] + cd2 * Dk[l];
+          Dk[l] = d;
+          X[l] += tau * d;
+        }
+        if (!doMV) return;
+        if (repl) {
+          for (int r = lane; r < h.C; r += 32) {
+            const uint32_t l = l0 + r;
+            const T q = c1 * VL[l] - c2 * Qk[l] - c3 * Qm[l];
+            Qm[l] = q;
+            qg[h.R + r] = q;
+          }
+          return;
+        }
+        T xi[JM], hx[JM];
+        block_hv_loc<T, JM>(vgk, VL + l0, DG + l0, low, h, xi, hx);   // xi = v_k
+        __syncwarp();                             // the block's reads of VL are done
+  #pragma unroll
         for (int j = 0; j < JM; ++j) {
           const int r = lane + 32 * j;
           if (j < h.J && r < h.C) {
             const uint32_t l = l0 + r;
             const T qo = Qk[l];
-            const T q = xi[j];
-            const T p = hx[j];
+            const T q = c1 * xi[j] - c2 * qo - c3 * Qm[l];
+            const T p = c1 * hx[j] - c2 * Pk[l] - c3 * Pm[l];
             const T v = MI[l] * p;
-            Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
+            Qm[l] = q; Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
             const T mq = MV[l] * q;
             a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
           }
         }
       });
+      if (!doMV) {                                // the last d/x update only
+        __syncthreads();
+        if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
+        __syncthreads();
+        break;
+      }
+      if (repl) {
+        // publish q_{k+1}, then p_{k+1} = (H - sigma) q_{k+1}
+        if (!(ok = reduce(a))) break;
+        each_block([&](const Hdr& h, uint32_t l0) {
+          T xi[JM], hx[JM];
+          block_hv_loc<T, JM>(qg, Qm + l0, DG + l0, low, h, xi, hx);  // xi = q_{k+1}
+  #pragma unroll
+          for (int j = 0; j < JM; ++j) {
+            const int r = lane + 32 * j;
+            if (j < h.J && r < h.C) {
+              const uint32_t l = l0 + r;
+              const T qo = Qk[l];
+              const T q = xi[j];
+              const T p = hx[j];
+              const T v = MI[l] * p;
+              Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
+              const T mq = MV[l] * q;
+              a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
+            }
+          }
+        });
+      }
+      if (!(ok = reduce(a))) break;
     }
-    if (!(ok = reduce(a))) break;
-  }
-  __syncthreads();
-  each_block([&](const Hdr& h, uint32_t l0) {
-    for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
-  });
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
-    *st = S;
+    __syncthreads();
+    each_block([&](const Hdr& h, uint32_t l0) {
+      for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
+    });
+    if (cta == 0 && threadIdx.x == 0) {
+      if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
+      *sj.st = S;
+    }
+    if (!ok) break;
   }
 }
+
+}  // namespace
 
 // Steps between replacements of p by a product: HS_MINRES_PIPE_R, else 20.
 // Measured at L = 14..18 (FP64, tolerance 1e-12, row norm): without
@@ -306,88 +354,67 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(
 // R = 20 1.0-1.9x (the two-reduction form 0.9-1.3x), at the same iteration
 // counts, wherever the two-reduction form reaches the tolerance; each
 // replacement costs one extra barrier.
-int replace_period() {
+int pipe_replace_period() {
   if (const char* e = getenv("HS_MINRES_PIPE_R")) return std::max(0, atoi(e));
   return 20;
 }
 
-// HS_CUDA (no message) when the form does not apply: no room in shared memory,
-// no cooperative launch, or the expansion of beta^2 was not trusted (the caller
-// then solves with the two-reduction form).
+namespace {
+
+// Launch for one or two queues; HS_CUDA without a message when it does not
+// fit in shared memory or the cooperative launch is refused.
 template <typename T, int PC, int JM, int NT>
-hs_status solve_v(hs_handle* hd, const T* b, const MinresVecs& v, double tol, long long kmax) {
-  const int bud = hd->sm_budget.load(std::memory_order_relaxed);
-  const int G = std::max(1, std::min(hd->num_sms, bud > 0 ? bud : hd->num_sms));
-  if (G > 256) return HS_CUDA;
-  int* first = nullptr;
-  int rows_cap = 0, hdr_cap = 0;
-  hs_status st = smr_plan(hd, G, &first, &rows_cap, &hdr_cap);
-  if (st != HS_OK) return st;
+hs_status launch1_t(int device, cudaStream_t s, const SmemJob& job0, const SmemQueue (&q)[2],
+                    const int (&ng)[2], const int (&hc)[2], int rperiod) {
   int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, hd->device);
-  const size_t sm = smr1_bytes<T>((int)hd->low.size(), hdr_cap, rows_cap, NT);
-  const size_t static_sm = sizeof(MinresState) + 24 * 8 + 64;
-  if (sm + static_sm > (size_t)optin) return HS_CUDA;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  size_t sm = smr1_bytes<T>(q[0].nlow, hc[0], q[0].rows_cap, NT);
+  if (ng[1] > 0) sm = std::max(sm, smr1_bytes<T>(q[1].nlow, hc[1], q[1].rows_cap, NT));
+  if (sm + SMEM_STATIC_BYTES > (size_t)optin) return HS_CUDA;
   if (cudaFuncSetAttribute(k_minres_smem1<T, PC, JM, NT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
     cudaGetLastError();
     return HS_CUDA;
   }
-  Geo g = hd->geo();
-  int* err = reinterpret_cast<int*>(hd->d_counter + 10);
-  HS_CUDA_TRY(hd, cudaMemsetAsync(hd->d_counter + 10, 0, sizeof(unsigned), hd->stream));
-  // generations start from zero for every solve
-  SlotN* slots = reinterpret_cast<SlotN*>(hd->d_partial);
-  HS_CUDA_TRY(hd, cudaMemsetAsync(slots, 0, 2 * sizeof(SlotN) * G, hd->stream));
-  const double* ds = hd->d_sigma;
-  MinresState* stp = hd->d_state;
-  unsigned long long limit = 1ull << 22;
-  if (const char* e = getenv("HS_BARRIER_LIMIT")) limit = strtoull(e, nullptr, 10);
-  int rp = replace_period();
-  T* vg0 = (T*)v.q0;
-  T* vg1 = (T*)v.q1;
-  T* qg = (T*)v.p;
-  T* xo = (T*)v.x;
-  void* args[] = {&g, (void*)&b, &vg0, &vg1, &qg, &xo, &stp, &tol, &kmax, &rp, (void*)&ds,
-                  &slots, &err, &limit, &first, &rows_cap};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_minres_smem1<T, PC, JM, NT>, dim3(G),
-                                              dim3(NT), args, sm, hd->stream);
+  SmemJob j = job0;
+  SmemQueue q0 = q[0], q1 = ng[1] > 0 ? q[1] : q[0];
+  int ctas0 = ng[0] * q[0].S;
+  int rp = rperiod;
+  void* args[] = {&j, &q0, &q1, &ctas0, &rp};
+  const int grid = ctas0 + (ng[1] > 0 ? ng[1] * q[1].S : 0);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_minres_smem1<T, PC, JM, NT>,
+                                                    dim3(grid), dim3(NT), args, sm, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return HS_CUDA;
   }
   count_launches(1);
-  HS_CUDA_TRY(hd, cudaMemcpyAsync(hd->h_state, hd->d_state, sizeof(MinresState),
-                                  cudaMemcpyDeviceToHost, hd->stream));
-  HS_CUDA_TRY(hd, cudaStreamSynchronize(hd->stream));
-  const MinresState& S = *hd->h_state;
-  if (S.status == HS_BREAKDOWN && S.pad == PIPE_EXPANSION) return HS_CUDA;
   return HS_OK;
 }
 
+// blocks of at most 96 rows (k <= 8, every chain up to L = 20): 3 rows per
+// lane; larger blocks 8 rows per lane and 256 threads (a few blocks per CTA
+// at most, and no register spills in FP64)
 template <typename T, int PC>
-hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, long long kmax) {
-  // blocks of at most 96 rows (k <= 8, every chain up to L = 20): 3 rows per
-  // lane; larger blocks 8 rows per lane and 256 threads (a few blocks per CTA
-  // at most, and no register spills in FP64)
-  if (hd->k <= 8) return solve_v<T, PC, 3, 512>(hd, b, v, tol, kmax);
-  return solve_v<T, PC, JMAX, 256>(hd, b, v, tol, kmax);
+hs_status launch1_pc(int k, int device, cudaStream_t s, const SmemJob& job0,
+                     const SmemQueue (&q)[2], const int (&ng)[2], const int (&hc)[2],
+                     int rperiod) {
+  if (k <= 8) return launch1_t<T, PC, 3, 512>(device, s, job0, q, ng, hc, rperiod);
+  return launch1_t<T, PC, JMAX, 256>(device, s, job0, q, ng, hc, rperiod);
 }
 
 }  // namespace
 
-hs_status minres_solve_pipe(hs_handle* hd, const void* b, const MinresVecs& v, hs_dtype dt,
-                            int pc, double tol, long long kmax) {
-  if (dt == HS_F64) {
-    const double* bb = (const double*)b;
-    return pc == 0 ? solve_t<double, 0>(hd, bb, v, tol, kmax)
-         : pc == 1 ? solve_t<double, 1>(hd, bb, v, tol, kmax)
-                   : solve_t<double, 2>(hd, bb, v, tol, kmax);
-  }
-  const float* bb = (const float*)b;
-  return pc == 0 ? solve_t<float, 0>(hd, bb, v, tol, kmax)
-       : pc == 1 ? solve_t<float, 1>(hd, bb, v, tol, kmax)
-                 : solve_t<float, 2>(hd, bb, v, tol, kmax);
+hs_status launch_smem1(hs_dtype dt, int pc, int k, int device, cudaStream_t s,
+                       const SmemJob& job0, const SmemQueue (&q)[2], const int (&ng)[2],
+                       const int (&hc)[2], int rperiod) {
+  if (dt == HS_F64)
+    return pc == 0 ? launch1_pc<double, 0>(k, device, s, job0, q, ng, hc, rperiod)
+         : pc == 1 ? launch1_pc<double, 1>(k, device, s, job0, q, ng, hc, rperiod)
+                   : launch1_pc<double, 2>(k, device, s, job0, q, ng, hc, rperiod);
+  return pc == 0 ? launch1_pc<float, 0>(k, device, s, job0, q, ng, hc, rperiod)
+       : pc == 1 ? launch1_pc<float, 1>(k, device, s, job0, q, ng, hc, rperiod)
+                 : launch1_pc<float, 2>(k, device, s, job0, q, ng, hc, rperiod);
 }
 
 }  // namespace hs

@@ -18,11 +18,6 @@ struct MinresVecs {
 hs_status minres_solve_sb(hs_handle* hd, const void* b, const MinresVecs& v, hs_dtype dt,
                           int pc, double tol, long long kmax, bool* used);
 
-// minres_pipe.cu: the one-reduction shared-memory form (pc as above). HS_CUDA
-// without a message where it does not apply (then nothing was written to x).
-hs_status minres_solve_pipe(hs_handle* hd, const void* b, const MinresVecs& v, hs_dtype dt,
-                            int pc, double tol, long long kmax);
-
 // Scalar part of pass B (Givens rotation of Algorithm 2), on one thread.
 __device__ __forceinline__ void givens_update(MinresState& S, double sumsq) {
   const double bn = sumsq >= 0.0 ? sqrt(sumsq) : NAN;        // beta_{k+1}

@@ -158,15 +158,15 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
 // Slot reduction for grids of at most 256 CTAs, called by warp 0 with the
 // CTA's totals in (c0, c1): publish, poll every slot with independent relaxed
 // loads, one acquire fence, then a fixed-order sum (identical in every CTA).
-__device__ __forceinline__ bool slot_reduce_w0(Slot* slots, int G, unsigned gen, double c0,
-                                               double c1, double (&tot)[2],
+__device__ __forceinline__ bool slot_reduce_w0(Slot* slots, int G, int cta, unsigned gen,
+                                               double c0, double c1, double (&tot)[2],
                                                unsigned long long limit, int* err) {
   const int lane = threadIdx.x & 31;
   Slot* buf = slots + (size_t)(gen & 1u) * G;
   if (lane == 0) {
-    buf[blockIdx.x].v0 = c0;
-    buf[blockIdx.x].v1 = c1;
-    st_release_u32(&buf[blockIdx.x].gen, gen);   // orders the partials and, after the
+    buf[cta].v0 = c0;
+    buf[cta].v1 = c1;
+    st_release_u32(&buf[cta].gen, gen);   // orders the partials and, after the
   }                                              // CTA barrier, the CTA's vector stores
   int ok = 1;
   unsigned long long it = 0;
@@ -306,15 +306,15 @@ __device__ __forceinline__ void cta_sumN(const T (&a)[NV], int nact, double* stm
 // (bounded by limit), one acquire fence, then a fixed-order sum so that every
 // CTA ends with identical totals in tot (all lanes).
 template <int NV>
-__device__ __forceinline__ bool slot_reduceN_w0(SlotN* slots, int G, unsigned gen, const double* c,
-                                                double (&tot)[NV], unsigned long long limit,
-                                                int* err) {
+__device__ __forceinline__ bool slot_reduceN_w0(SlotN* slots, int G, int cta, unsigned gen,
+                                                const double* c, double (&tot)[NV],
+                                                unsigned long long limit, int* err) {
   const int lane = threadIdx.x & 31;
   SlotN* buf = slots + (size_t)(gen & 1u) * G;
   if (lane == 0) {
 #pragma unroll
-    for (int j = 0; j < NV; ++j) buf[blockIdx.x].v[j] = c[j];
-    st_release_u32(&buf[blockIdx.x].gen, gen);
+    for (int j = 0; j < NV; ++j) buf[cta].v[j] = c[j];
+    st_release_u32(&buf[cta].gen, gen);
   }
   int ok = 1;
   unsigned long long it = 0;
@@ -353,6 +353,70 @@ __device__ __forceinline__ bool slot_reduceN_w0(SlotN* slots, int G, unsigned ge
   }
   return __all_sync(0xffffffffu, ok) != 0;
 }
+
+// One solve of a job queue: the realisation's geometry, right-hand side and
+// solution (device, n elements of the solver's type), final state and
+// parameters.
+struct SmemJob {
+  Geo g;
+  const void* b;
+  void* x;
+  MinresState* st;
+  double sigma, tol;
+  long long kmax;
+};
+
+// Static shared memory of the shared-memory kernels (state, job, scalars),
+// with a margin, for the fit check against the opt-in limit.
+constexpr size_t SMEM_STATIC_BYTES = sizeof(MinresState) + sizeof(SmemJob) + 32 * 8 + 64;
+
+// A job queue of a shared-memory solver launch: groups of S CTAs, each taking
+// jobs until the queue is empty (head[0]: next job, atomic; head[1]: number of
+// jobs, both set before the launch); jobs == nullptr runs the kernel parameter
+// job0 alone, with one group. All jobs of a queue have the same L (one block
+// plan, cta_first, for the S CTAs of any group; nlow low-table entries).
+// slots: 2 S reduction slots per group; w[0..2]: the group's global vectors
+// for the gathers, group g at w[i] + g ws_stride elements. Waits give up after
+// limit polls and set *err. A launch serves up to two queues (two chain
+// lengths): its first ctas0 CTAs take queue 0, the rest queue 1.
+struct SmemQueue {
+  const SmemJob* jobs;
+  int* head;
+  int S;
+  int nlow;
+  void* slots;
+  int* err;
+  unsigned long long limit;
+  const int* cta_first;
+  int rows_cap;
+  void* w[3];
+  long long ws_stride;
+};
+
+// MinresState.pad of a one-reduction solve that ended because the expansion
+// of beta_{k+1}^2 cancelled to rounding level (status HS_BREAKDOWN): the solve
+// is to be redone by the two-reduction form.
+constexpr int PIPE_EXPANSION = 1;
+
+// Launches of the two-reduction (minres.cu) and one-reduction (minres_pipe.cu)
+// kernels (k: low bits of the block layout). Asynchronous on s; HS_CUDA
+// without a message when the form does not fit in shared memory or the
+// cooperative launch is refused.
+// ngroups[i] groups of q[i].S CTAs serve queue i (ngroups[1] = 0: one queue);
+// hdr_cap[i]: most blocks per CTA of queue i's plan; smem is sized for the
+// larger of the two layouts.
+hs_status launch_smem2(hs_dtype dt, int pc, int k, int device, cudaStream_t s,
+                       const SmemJob& job0, const SmemQueue (&q)[2], const int (&ngroups)[2],
+                       const int (&hdr_cap)[2]);
+hs_status launch_smem1(hs_dtype dt, int pc, int k, int device, cudaStream_t s,
+                       const SmemJob& job0, const SmemQueue (&q)[2], const int (&ngroups)[2],
+                       const int (&hdr_cap)[2], int rperiod);
+int pipe_replace_period();
+
+// One solve of the handle in a shared-memory form (minres.cu): one job, one
+// group of all the handle's SMs; x in v.x and the state in hd->h_state.
+hs_status solve_smem_job(hs_handle* hd, const void* b, const MinresVecs& v, hs_dtype dt, int pc,
+                         double tol, long long kmax, bool one);
 
 // Contiguous block ranges per CTA with balanced row counts, cached per grid
 // size (minres.cu).
