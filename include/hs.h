@@ -203,6 +203,51 @@ hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_m
                        int sm_budget, double* evals_host, double* evecs_host,
                        double* resid_host, double* z_host, hs_lanczos_info* info);
 
+/* Batched disorder sweep (Sec. IV B-C: |z|^2 averaged within each realisation,
+ * then across realisations). B realisations, L_host[r] (even, 4..32, at most
+ * two distinct values) and fields h_host (the realisations' L_host[r] values
+ * concatenated in order), each with sigma = (E_min + E_max) / 2 and the start
+ * vector of seed + r. Algorithm 1 runs in lockstep rounds with FP64 inner
+ * solves (Algorithm 2, pc, relative tolerance minres_tol, at most 50 n
+ * iterations); each round's solves go to one persistent cooperative launch
+ * whose CTA groups take them from one job queue per chain length, replayed
+ * from a CUDA graph when capture succeeds. Group size and form per (L, pc, SM
+ * count) are timed on first use and cached in the JSON file HS_SWEEP_TUNE
+ * (default $HOME/.cache/hs_sweep_tune.json); HS_SWEEP_S / HS_SWEEP_FORM
+ * (1 = one-reduction, 2 = two-reduction) force them.
+ * Outputs (host, realisation r at offset r K): evals_host (B K, each ordered as
+ * by hs_lanczos_eigs), resid_host (B K FP64 residuals ||H psi - E psi||, may be
+ * NULL), z_host (2 B K: Re, Im of the twist overlaps, may be NULL), zz_host (B:
+ * the mean of |z|^2 over the realisation's K pairs, may be NULL).
+ * HS_NOT_CONVERGED (outputs written) when some realisation's pairs did not
+ * converge; other errors leave the outputs undefined. Uses the current device;
+ * allocates its own stream, handles and workspace and frees them. */
+typedef struct {
+  int realisations;      /* B                                                      */
+  int converged;         /* realisations whose K pairs all converged               */
+  int rounds;            /* lockstep Lanczos rounds                                */
+  int launches;          /* solver launches (graph replays included)               */
+  int graph;             /* 1: the rounds were replayed from a captured CUDA graph */
+  int nclass;            /* distinct chain lengths (1 or 2)                        */
+  long long minres_iters;
+  int L[2];              /* per chain length: L,                                   */
+  int S[2];              /*   CTAs per group,                                      */
+  int groups[2];         /*   groups,                                              */
+  int form[2];           /*   solver form (HS_FORM_SMEM or HS_FORM_SMEM1),         */
+  int tuned[2];          /*   1 timed now, 0 from the cache, -1 forced             */
+  double zz_mean[2];     /*   mean over realisations of the per-realisation mean   */
+  double zz_std[2];      /*   of |z|^2, and its sample standard deviation          */
+  double max_resid;      /* largest FP64 residual of all pairs                     */
+  double seconds_setup;  /* handles, sigma, start vectors, schedule                */
+  double seconds_solve;  /* the rounds                                             */
+  double seconds_total;
+} hs_sweep_info;
+
+hs_status hs_sweep(int B, const int* L_host, const double* h_host, int K, int m_max, double tol,
+                   unsigned long long seed, double minres_tol, hs_precond pc,
+                   double* evals_host, double* resid_host, double* z_host, double* zz_host,
+                   hs_sweep_info* info);
+
 /* Twist overlap z_i = <psi_i| U_twist |psi_i>, U_twist = exp[i 2pi/L sum_j j Sz_j]
  * (Sec. III), for K real FP64 vectors psi_dev + i n (not normalised by the
  * call). z_host[2 i] = Re z_i, z_host[2 i + 1] = Im z_i. */

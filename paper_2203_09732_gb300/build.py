@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUTDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUTDIR, "libhs.so")
-SOURCES = ["api.cu", "hv.cu", "minres.cu", "vec.cu", "twist.cu", "lanczos.cu", "twist_noalloc.cu", "hv_sb.cu", "minres_sb.cu", "observables.cu", "adjoint.cu", "minres_pipe.cu"]
+SOURCES = ["api.cu", "hv.cu", "minres.cu", "vec.cu", "twist.cu", "lanczos.cu", "twist_noalloc.cu", "hv_sb.cu", "minres_sb.cu", "observables.cu", "adjoint.cu", "minres_pipe.cu", "sweep.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                 "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]

@@ -9,7 +9,7 @@
 #include <numeric>
 #include <vector>
 
-#include "common.cuh"
+#include "lanczos.cuh"
 
 namespace hs {
 
@@ -163,108 +163,117 @@ extern "C" hs_status hs_extremal(hs_handle* hd, int max_steps, double tol, doubl
   return HS_OK;
 }
 
-extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol,
-                                     unsigned long long seed, const double* v0_dev, int mixed,
-                                     hs_precond pc, double minres_tol, double inner_tol,
-                                     long long minres_kmax, double* evals_host,
-                                     double* evecs_dev, double* resid_host,
-                                     hs_lanczos_info* info) {
-  using clk = std::chrono::steady_clock;
-  const auto t0 = clk::now();
-  if (!hd) return HS_BAD_ARG;
+namespace hs {
+
+hs_status lz_start(LzRun& r, hs_handle* hd, int K, int m_max, double tol,
+                   unsigned long long seed, const double* v0_dev) {
+  r = LzRun();
+  r.t0 = std::chrono::steady_clock::now();
+  r.hd = hd;
   const long long n = hd->n;
-  if (K < 1 || K > n || !evals_host) return fail(hd, HS_BAD_ARG, "hs_lanczos_eigs: bad K or output");
-  if (!(tol > 0)) tol = 1e-10;
-  if (!(minres_tol > 0)) minres_tol = 1e-12;
-  const long long kcap = minres_kmax > 0 ? minres_kmax : 50 * n;
+  if (K < 1 || K > n) return fail(hd, HS_BAD_ARG, "hs_lanczos_eigs: bad K or output");
+  r.K = K;
+  r.tol = tol > 0 ? tol : 1e-10;
   int m = m_max > 0 ? m_max : std::max(130, 3 * K + 30);
   m = (int)std::min<long long>(m, n);
   if (m < K) m = K;
   if (m > 500) return fail(hd, HS_BAD_ARG, "m_max > 500");
   if (K * m > 4096 * 8) return fail(hd, HS_BAD_ARG, "K * m too large");
-  if (info) std::memset(info, 0, sizeof(*info));
+  r.m = m;
   // basis V (m + 1 vectors), x, w, scratch
   hs_status st = ensure_lz(hd, (size_t)m + 4);
   if (st != HS_OK) return st;
-  double* V = hd->lz;
-  double* x = hd->lz + (size_t)(m + 1) * n;
-  double* w = x + n;
-  double* tmp = w + n;
+  r.V = hd->lz;
+  r.x = hd->lz + (size_t)(m + 1) * n;
+  r.w = r.x + n;
+  r.tmp = r.w + n;
+  r.h.assign(m + 1, 0.0);
   double nn;
-  if (v0_dev) HS_CUDA_TRY(hd, cudaMemcpyAsync(V, v0_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, hd->stream));
-  else if ((st = vsplitmix(hd, seed, V, n)) != HS_OK) return st;
-  if ((st = vdot(hd, V, V, n, &nn)) != HS_OK) return st;
+  if (v0_dev) HS_CUDA_TRY(hd, cudaMemcpyAsync(r.V, v0_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, hd->stream));
+  else if ((st = vsplitmix(hd, seed, r.V, n)) != HS_OK) return st;
+  if ((st = vdot(hd, r.V, r.V, n, &nn)) != HS_OK) return st;
   if (!(nn > 0) || !std::isfinite(nn)) return fail(hd, HS_BAD_ARG, "start vector is zero or non-finite");
-  if ((st = vscale_to(hd, 1.0 / std::sqrt(nn), V, V, n)) != HS_OK) return st;
-  std::vector<double> alpha, beta;   // beta[j] = beta_{j+2} couples j, j+1
-  std::vector<double> h(m + 1);
-  double solve_s = 0.0;
-  int steps = 0, nconv = 0;
-  double beta_k = 0.0;               // beta_k multiplying v_{k-1}
-  std::vector<double> theta, Y;
-  hs_minres_info mi;
-  for (int k = 0; k < m; ++k) {
-    double* vk = V + (size_t)k * n;
-    const auto ts = clk::now();
-    std::memset(&mi, 0, sizeof(mi));
-    if (mixed) st = minres_mixed(hd, vk, x, minres_tol, kcap, pc, inner_tol > 0 ? inner_tol : 1e-5, &mi);
-    else st = minres_solve64(hd, vk, x, minres_tol, kcap, pc, &mi);
-    solve_s += std::chrono::duration<double>(clk::now() - ts).count();
-    if (info) { info->minres_iters += mi.iters; info->sweeps += mixed ? mi.sweeps : 1; }
-    if (st != HS_OK && st != HS_NOT_CONVERGED) return st;
-    // a solve that hit its iteration cap feeds an inexact (H - sigma)^-1 v_k
-    // into the recurrence; the final FP64 residuals still certify the pairs,
-    // and the count is reported
-    if (st == HS_NOT_CONVERGED && info) ++info->unconverged_solves;
-    // w = x - beta_k v_{k-1}; alpha_k = v_k . w; w -= alpha_k v_k
-    HS_CUDA_TRY(hd, cudaMemcpyAsync(w, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, hd->stream));
-    if (k > 0 && (st = vaxpby(hd, -beta_k, V + (size_t)(k - 1) * n, 1.0, w, n)) != HS_OK) return st;
-    double al;
-    if ((st = vdot(hd, vk, w, n, &al)) != HS_OK) return st;
-    if ((st = vaxpby(hd, -al, vk, 1.0, w, n)) != HS_OK) return st;
-    // full reorthogonalisation against v_1..v_k, two classical Gram-Schmidt passes
-    for (int pass = 0; pass < 2; ++pass) {
-      if ((st = vmultidot(hd, V, k + 1, w, n, h.data())) != HS_OK) return st;
-      if ((st = vmultiaxpy(hd, V, k + 1, h.data(), w, n)) != HS_OK) return st;
-    }
-    double bb;
-    if ((st = vdot(hd, w, w, n, &bb)) != HS_OK) return st;
-    const double bn = std::sqrt(bb);
-    alpha.push_back(al);
-    steps = k + 1;
-    // Ritz values of T_k and the residual estimates beta_{k+1} |y_{k,i}|
-    const int kk = steps;
-    if (kk >= K) {
-      theta.assign(kk, 0.0);
-      Y.assign((size_t)kk * kk, 0.0);
-      if ((st = tridiag_eig(kk, alpha.data(), beta.data(), theta.data(), Y.data())) != HS_OK)
-        return fail(hd, st, "tridiagonal eigensolver did not converge");
-      std::vector<int> ord(kk);
-      std::iota(ord.begin(), ord.end(), 0);
-      std::stable_sort(ord.begin(), ord.end(),
-                       [&](int a, int b) { return std::fabs(theta[a]) > std::fabs(theta[b]); });
-      nconv = 0;
-      for (int q = 0; q < K; ++q) {
-        const int i = ord[q];
-        const double est = bn * std::fabs(Y[(size_t)i * kk + kk - 1]);
-        if (est <= tol * std::fabs(theta[i])) ++nconv;
-      }
-    }
-    if (nconv == K || bn <= 1e-13 * std::fabs(al) || k + 1 == m) break;
-    beta.push_back(bn);
-    if ((st = vscale_to(hd, 1.0 / bn, w, V + (size_t)(k + 1) * n, n)) != HS_OK) return st;
-    beta_k = bn;
+  return vscale_to(hd, 1.0 / std::sqrt(nn), r.V, r.V, n);
+}
+
+hs_status lz_step(LzRun& r, hs_status solve_status, long long iters, int sweeps) {
+  hs_handle* hd = r.hd;
+  const long long n = hd->n;
+  const int k = r.k;
+  r.minres_iters += iters;
+  r.sweeps += sweeps;
+  if (solve_status != HS_OK && solve_status != HS_NOT_CONVERGED) return solve_status;
+  // a solve that hit its iteration cap feeds an inexact (H - sigma)^-1 v_k
+  // into the recurrence; the final FP64 residuals still certify the pairs,
+  // and the count is reported
+  if (solve_status == HS_NOT_CONVERGED) ++r.unconverged_solves;
+  double* V = r.V;
+  double* vk = V + (size_t)k * n;
+  double* w = r.w;
+  hs_status st;
+  // w = x - beta_k v_{k-1}; alpha_k = v_k . w; w -= alpha_k v_k
+  HS_CUDA_TRY(hd, cudaMemcpyAsync(w, r.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, hd->stream));
+  if (k > 0 && (st = vaxpby(hd, -r.beta_k, V + (size_t)(k - 1) * n, 1.0, w, n)) != HS_OK) return st;
+  double al;
+  if ((st = vdot(hd, vk, w, n, &al)) != HS_OK) return st;
+  if ((st = vaxpby(hd, -al, vk, 1.0, w, n)) != HS_OK) return st;
+  // full reorthogonalisation against v_1..v_k, two classical Gram-Schmidt passes
+  for (int pass = 0; pass < 2; ++pass) {
+    if ((st = vmultidot(hd, V, k + 1, w, n, r.h.data())) != HS_OK) return st;
+    if ((st = vmultiaxpy(hd, V, k + 1, r.h.data(), w, n)) != HS_OK) return st;
   }
+  double bb;
+  if ((st = vdot(hd, w, w, n, &bb)) != HS_OK) return st;
+  const double bn = std::sqrt(bb);
+  r.alpha.push_back(al);
+  r.steps = k + 1;
+  // Ritz values of T_k and the residual estimates beta_{k+1} |y_{k,i}|
+  const int kk = r.steps;
+  if (kk >= r.K) {
+    r.theta.assign(kk, 0.0);
+    r.Y.assign((size_t)kk * kk, 0.0);
+    if ((st = tridiag_eig(kk, r.alpha.data(), r.beta.data(), r.theta.data(), r.Y.data())) != HS_OK)
+      return fail(hd, st, "tridiagonal eigensolver did not converge");
+    std::vector<int> ord(kk);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int a, int b) { return std::fabs(r.theta[a]) > std::fabs(r.theta[b]); });
+    r.nconv = 0;
+    for (int q = 0; q < r.K; ++q) {
+      const int i = ord[q];
+      const double est = bn * std::fabs(r.Y[(size_t)i * kk + kk - 1]);
+      if (est <= r.tol * std::fabs(r.theta[i])) ++r.nconv;
+    }
+  }
+  if (r.nconv == r.K || bn <= 1e-13 * std::fabs(al) || k + 1 == r.m) {
+    r.done = true;
+    return HS_OK;
+  }
+  r.beta.push_back(bn);
+  if ((st = vscale_to(hd, 1.0 / bn, w, V + (size_t)(k + 1) * n, n)) != HS_OK) return st;
+  r.beta_k = bn;
+  r.k = k + 1;
+  return HS_OK;
+}
+
+hs_status lz_finish(LzRun& r, double* evals_host, double* evecs_dev, double* resid_host,
+                    hs_lanczos_info* info) {
+  using clk = std::chrono::steady_clock;
+  hs_handle* hd = r.hd;
+  const long long n = hd->n;
+  const int K = r.K;
+  hs_status st;
   // Ritz pairs: K largest |theta|, then ordered by |E - sigma| (ties by E)
   const auto tr = clk::now();
-  const int kk = steps;
+  const int kk = r.steps;
+  if (kk < K) return fail(hd, HS_NOT_CONVERGED, "Lanczos stopped before K steps");
   std::vector<int> ord(kk);
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(),
-                   [&](int a, int b) { return std::fabs(theta[a]) > std::fabs(theta[b]); });
+                   [&](int a, int b) { return std::fabs(r.theta[a]) > std::fabs(r.theta[b]); });
   ord.resize(K);
   std::vector<double> Ew(K);
-  for (int q = 0; q < K; ++q) Ew[q] = hd->sigma + 1.0 / theta[ord[q]];
+  for (int q = 0; q < K; ++q) Ew[q] = hd->sigma + 1.0 / r.theta[ord[q]];
   std::vector<int> o2(K);
   std::iota(o2.begin(), o2.end(), 0);
   std::stable_sort(o2.begin(), o2.end(), [&](int a, int b) {
@@ -273,12 +282,13 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
   });
   std::vector<double> Ysel((size_t)K * kk);
   for (int q = 0; q < K; ++q)
-    std::memcpy(&Ysel[(size_t)q * kk], &Y[(size_t)ord[o2[q]] * kk], sizeof(double) * kk);
+    std::memcpy(&Ysel[(size_t)q * kk], &r.Y[(size_t)ord[o2[q]] * kk], sizeof(double) * kk);
   // psi = V_k Y (into evecs_dev, or one vector at a time into tmp)
   double max_res = 0.0;
+  double* w = r.w;
   for (int q = 0; q < K; ++q) {
-    double* psi = evecs_dev ? evecs_dev + (size_t)q * n : tmp;
-    if ((st = vritz(hd, V, kk, &Ysel[(size_t)q * kk], 1, psi, n)) != HS_OK) return st;
+    double* psi = evecs_dev ? evecs_dev + (size_t)q * n : r.tmp;
+    if ((st = vritz(hd, r.V, kk, &Ysel[(size_t)q * kk], 1, psi, n)) != HS_OK) return st;
     double pp, pHp, HH;
     if ((st = launch_matvec(hd, psi, w, HS_F64, 0)) != HS_OK) return st;
     if ((st = vdot(hd, psi, psi, n, &pp)) != HS_OK) return st;
@@ -294,19 +304,54 @@ extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol
     max_res = std::max(max_res, res);
   }
   if (info) {
-    info->steps = steps;
-    info->converged = nconv;
+    info->steps = r.steps;
+    info->converged = r.nconv;
+    info->minres_iters = r.minres_iters;
+    info->sweeps = r.sweeps;
+    info->unconverged_solves = r.unconverged_solves;
     info->sigma = hd->sigma;
     info->max_resid = max_res;
-    info->seconds_solve = solve_s;
-    info->seconds_total = std::chrono::duration<double>(clk::now() - t0).count();
+    info->seconds_solve = r.solve_s;
+    info->seconds_total = std::chrono::duration<double>(clk::now() - r.t0).count();
     info->seconds_ritz = std::chrono::duration<double>(clk::now() - tr).count();
   }
-  if (nconv < K) {
+  if (r.nconv < K) {
     hd->err = "Lanczos reached m_max before all wanted pairs converged";
     return HS_NOT_CONVERGED;
   }
   return HS_OK;
+}
+
+}  // namespace hs
+
+extern "C" hs_status hs_lanczos_eigs(hs_handle* hd, int K, int m_max, double tol,
+                                     unsigned long long seed, const double* v0_dev, int mixed,
+                                     hs_precond pc, double minres_tol, double inner_tol,
+                                     long long minres_kmax, double* evals_host,
+                                     double* evecs_dev, double* resid_host,
+                                     hs_lanczos_info* info) {
+  using clk = std::chrono::steady_clock;
+  if (!hd) return HS_BAD_ARG;
+  if (!evals_host) return fail(hd, HS_BAD_ARG, "hs_lanczos_eigs: bad K or output");
+  if (!(minres_tol > 0)) minres_tol = 1e-12;
+  const long long kcap = minres_kmax > 0 ? minres_kmax : 50 * hd->n;
+  if (info) std::memset(info, 0, sizeof(*info));
+  LzRun r;
+  hs_status st = lz_start(r, hd, K, m_max, tol, seed, v0_dev);
+  if (st != HS_OK) return st;
+  hs_minres_info mi;
+  while (!r.done) {
+    const auto ts = clk::now();
+    std::memset(&mi, 0, sizeof(mi));
+    if (mixed) st = minres_mixed(hd, r.rhs(), r.x, minres_tol, kcap, pc, inner_tol > 0 ? inner_tol : 1e-5, &mi);
+    else st = minres_solve64(hd, r.rhs(), r.x, minres_tol, kcap, pc, &mi);
+    r.solve_s += std::chrono::duration<double>(clk::now() - ts).count();
+    if ((st = lz_step(r, st, mi.iters, mixed ? mi.sweeps : 1)) != HS_OK) {
+      if (info) { info->minres_iters = r.minres_iters; info->sweeps = r.sweeps; }
+      return st;
+    }
+  }
+  return lz_finish(r, evals_host, evecs_dev, resid_host, info);
 }
 
 extern "C" hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_max,

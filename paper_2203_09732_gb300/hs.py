@@ -28,7 +28,7 @@ SYMBOLS = ["hs_create", "hs_free", "hs_last_error", "hs_dim", "hs_get_sigma", "h
            "hs_extremal", "hs_unrank", "hs_rank", "hs_diag", "hs_matvec", "hs_minres",
            "hs_minres_f32", "hs_lanczos_eigs", "hs_eigs_host", "hs_twist", "hs_tridiag_eig",
            "hs_kernel_launches", "hs_set_sm_budget", "hs_twist_noalloc", "hs_entanglement",
-           "hs_level_ratio", "hs_sym_eigvals", "hs_twist_grad"]
+           "hs_level_ratio", "hs_sym_eigvals", "hs_twist_grad", "hs_sweep"]
 
 
 class MinresInfo(ctypes.Structure):
@@ -50,6 +50,24 @@ class LanczosInfo(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class SweepInfo(ctypes.Structure):
+    _fields_ = [("realisations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("rounds", ctypes.c_int), ("launches", ctypes.c_int), ("graph", ctypes.c_int),
+                ("nclass", ctypes.c_int), ("minres_iters", ctypes.c_longlong),
+                ("L", ctypes.c_int * 2), ("S", ctypes.c_int * 2), ("groups", ctypes.c_int * 2),
+                ("form", ctypes.c_int * 2), ("tuned", ctypes.c_int * 2),
+                ("zz_mean", ctypes.c_double * 2), ("zz_std", ctypes.c_double * 2),
+                ("max_resid", ctypes.c_double), ("seconds_setup", ctypes.c_double),
+                ("seconds_solve", ctypes.c_double), ("seconds_total", ctypes.c_double)]
+
+    def as_dict(self):
+        out = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            out[f] = list(v)[: self.nclass] if isinstance(v, ctypes.Array) else v
+        return out
 
 
 class HSError(RuntimeError):
@@ -107,6 +125,9 @@ def load(path=LIB_PATH):
                            ctypes.POINTER(MinresInfo)], ctypes.c_int),
         "hs_level_ratio": ([c_dp, ctypes.c_int, c_dp, c_dp], ctypes.c_int),
         "hs_sym_eigvals": ([ctypes.c_int, c_dp, c_dp], ctypes.c_int),
+        "hs_sweep": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), c_dp, ctypes.c_int, ctypes.c_int,
+                      ctypes.c_double, ctypes.c_ulonglong, ctypes.c_double, ctypes.c_int, c_dp,
+                      c_dp, c_dp, c_dp, ctypes.POINTER(SweepInfo)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -363,6 +384,31 @@ class Chain:
         z = np.zeros(2 * K)
         self._check(self._lib.hs_twist(self._hd, _ptr(psi), K, _dp(z)), "hs_twist")
         return z[0::2] + 1j * z[1::2]
+
+
+def sweep(Ls, hs_list, K, m_max=0, tol=1e-10, seed=0, minres_tol=1e-12, precond="row"):
+    """Batched disorder sweep (hs_sweep): realisation r has chain length Ls[r]
+    and fields hs_list[r]. Returns (evals (B, K), resid (B, K), z (B, K)
+    complex, zz (B,) = mean |z|^2 per realisation, info dict)."""
+    lib = load()
+    B = len(Ls)
+    if len(hs_list) != B:
+        raise ValueError("one field array per realisation")
+    Larr = (ctypes.c_int * B)(*[int(L) for L in Ls])
+    hh = np.ascontiguousarray(np.concatenate([np.asarray(h, dtype=np.float64) for h in hs_list]))
+    if any(len(h) != L for h, L in zip(hs_list, Ls)):
+        raise ValueError("len(h) must equal L for every realisation")
+    ev = np.zeros(B * K)
+    res = np.zeros(B * K)
+    z = np.zeros(2 * B * K)
+    zz = np.zeros(B)
+    info = SweepInfo()
+    st = lib.hs_sweep(B, Larr, _dp(hh), K, m_max, tol, seed, minres_tol, PRECOND[precond], _dp(ev),
+                      _dp(res), _dp(z), _dp(zz), ctypes.byref(info))
+    if st not in (HS_OK, HS_NOT_CONVERGED):
+        raise HSError(st, "hs_sweep")
+    zc = (z[0::2] + 1j * z[1::2]).reshape(B, K)
+    return ev.reshape(B, K), res.reshape(B, K), zc, zz, info.as_dict()
 
 
 def eigs_host(L, h, K, sigma=float("nan"), m_max=0, tol=1e-10, seed=0, mixed=True, precond="row",

@@ -115,3 +115,19 @@ def test_sym_eigvals_matches_numpy(lib):
         assert np.abs(w - np.linalg.eigvalsh(R)).max() <= 1e-12 * max(1.0, np.trace(R))
     D = np.diag([3.0, -1.0, 2.0])
     assert np.allclose(hs.sym_eigvals(D), [-1.0, 2.0, 3.0], atol=1e-15)
+
+
+def test_sweep_rejects_bad_arguments(lib):
+    """hs_sweep checks its arguments before any device work: no realisation,
+    three chain lengths, an odd L."""
+    import ctypes
+    from paper_2203_09732_gb300 import hs
+    info = hs.SweepInfo()
+    ev = np.zeros(8)
+    for Ls in ([], [8, 10, 12], [9]):
+        B = len(Ls)
+        Larr = (ctypes.c_int * max(B, 1))(*(Ls or [8]))
+        h = np.zeros(max(sum(Ls), 1))
+        st = lib.hs_sweep(B, Larr, h.ctypes.data_as(hs.c_dp), 2, 0, 1e-10, 0, 1e-12, 2,
+                          ev.ctypes.data_as(hs.c_dp), None, None, None, ctypes.byref(info))
+        assert st == hs.HS_BAD_ARG
