@@ -150,12 +150,16 @@ def parse():
                     help="skip the iteration-model solves (value then null)")
     ap.add_argument("--static-budget", action="store_true", dest="static_budget")
     ap.add_argument("--detail", default=None, help="write per-step records to this JSON file")
-    ap.add_argument("--only", choices=["hv", "minres", "forms", "smem"], default=None,
+    ap.add_argument("--sweep", default="24,0",
+                    help="--only sweep: realisations at L = 16 and L = 18 (C3 recipe)")
+    ap.add_argument("--only", choices=["hv", "minres", "forms", "smem", "sweep"], default=None,
                     help="profiling cases: only the H x timing at --L; one capped MINRES "
                          "solve (FP32 + refinement) of --minres-iters iterations at --L; the "
                          "products and MINRES iterations of every row form at L = 24, 26, 28; "
-                         "or --minres-iters FP64 and FP32 iterations of the one- and "
-                         "two-reduction shared-memory forms at --L (L <= 20)")
+                         "--minres-iters FP64 and FP32 iterations of the one- and "
+                         "two-reduction shared-memory forms at --L (L <= 20); or one batched "
+                         "sweep (hs_sweep) of the --sweep realisations, K = 8, beside the "
+                         "24-stream batch of the same L = 16 realisations")
     ap.add_argument("--minres-iters", type=int, default=200, dest="minres_iters")
     return ap.parse_args()
 
@@ -812,6 +816,28 @@ def smem_forms(torch, hs, inputs, L, iters):
     return out
 
 
+def sweep_case(torch, hs, args):
+    """One hs_sweep call over the C3-recipe realisations (h ~ U[0.5, 6],
+    h_j ~ U[-h, h]; the same realisations as the 24-stream batch), K = 8,
+    FP64 inner solves to --minres-tol: eigenpairs per second of the whole call
+    and of its rounds, with the schedule the library chose."""
+    n16, n18 = (int(v) for v in args.sweep.split(","))
+    K = 8
+    Ls, hl = [], []
+    for L, cnt in ((16, n16), (18, n18)):
+        for idx in range(cnt):
+            Ls.append(L)
+            hl.append(realisation(idx, L)[2])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev, res, z, zz, info = hs.sweep(Ls, hl, K, minres_tol=args.minres_tol)
+    sec = time.perf_counter() - t0
+    return {"value": K * len(Ls) / sec, "unit": UNIT, "seconds": sec,
+            "eigenpairs_per_s_rounds": K * len(Ls) / info["seconds_solve"],
+            "realisations": {"16": n16, "18": n18}, "K": K,
+            "max_resid": float(res.max()), "info": info}
+
+
 def run_only(args):
     """Single-kernel cases for profiler captures."""
     import torch
@@ -823,6 +849,13 @@ def run_only(args):
         return
     if args.only == "smem":
         print(json.dumps(smem_forms(torch, hs, inputs, args.L, args.minres_iters)))
+        return
+    if args.only == "sweep":
+        out = {"sweep": sweep_case(torch, hs, args)}
+        n16 = int(args.sweep.split(",")[0])
+        if n16 == BATCH and int(args.sweep.split(",")[1]) == 0:
+            out["streams_24"] = l16_batch(torch, hs, args)
+        print(json.dumps(out))
         return
     if args.only == "hv":
         rf = hv_roofline(torch, hs, args.L, torch.cuda.current_stream())

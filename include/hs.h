@@ -207,39 +207,39 @@ hs_status hs_eigs_host(int L, const double* h_host, double sigma, int K, int m_m
  * then across realisations). B realisations, L_host[r] (even, 4..32, at most
  * two distinct values) and fields h_host (the realisations' L_host[r] values
  * concatenated in order), each with sigma = (E_min + E_max) / 2 and the start
- * vector of seed + r. Algorithm 1 runs in lockstep rounds with FP64 inner
- * solves (Algorithm 2, pc, relative tolerance minres_tol, at most 50 n
- * iterations); each round's solves go to one persistent cooperative launch
- * whose CTA groups take them from one job queue per chain length, replayed
- * from a CUDA graph when capture succeeds. Group size and form per (L, pc, SM
- * count) are timed on first use and cached in the JSON file HS_SWEEP_TUNE
- * (default $HOME/.cache/hs_sweep_tune.json); HS_SWEEP_S / HS_SWEEP_FORM
- * (1 = one-reduction, 2 = two-reduction) force them.
+ * vector of seed + r. One persistent cooperative launch runs them all: CTA
+ * groups take realisations from one queue per chain length and run all of
+ * Algorithm 1 on each on the device (FP64 inner solves by Algorithm 2 with pc,
+ * relative tolerance minres_tol, at most 50 n iterations; full
+ * reorthogonalisation; the convergence test on T_k); m (m_max, else
+ * max(130, 3K + 30)) is at most 256. The group size per (L, pc, SM count) is
+ * timed on first use and cached in the JSON file HS_SWEEP_TUNE (default
+ * $HOME/.cache/hs_sweep_tune.json); HS_SWEEP_S forces it.
  * Outputs (host, realisation r at offset r K): evals_host (B K, each ordered as
- * by hs_lanczos_eigs), resid_host (B K FP64 residuals ||H psi - E psi||, may be
- * NULL), z_host (2 B K: Re, Im of the twist overlaps, may be NULL), zz_host (B:
- * the mean of |z|^2 over the realisation's K pairs, may be NULL).
+ * by hs_lanczos_eigs and certified the same way), resid_host (B K FP64
+ * residuals ||H psi - E psi||, may be NULL), z_host (2 B K: Re, Im of the twist
+ * overlaps, may be NULL), zz_host (B: the mean of |z|^2 over the realisation's
+ * K pairs, may be NULL).
  * HS_NOT_CONVERGED (outputs written) when some realisation's pairs did not
  * converge; other errors leave the outputs undefined. Uses the current device;
  * allocates its own stream, handles and workspace and frees them. */
 typedef struct {
   int realisations;      /* B                                                      */
   int converged;         /* realisations whose K pairs all converged               */
-  int rounds;            /* lockstep Lanczos rounds                                */
-  int launches;          /* solver launches (graph replays included)               */
-  int graph;             /* 1: the rounds were replayed from a captured CUDA graph */
+  int max_steps;         /* Lanczos steps of the longest realisation               */
+  int launches;          /* solver launches of the sweep (1)                       */
   int nclass;            /* distinct chain lengths (1 or 2)                        */
+  int pad;
   long long minres_iters;
   int L[2];              /* per chain length: L,                                   */
   int S[2];              /*   CTAs per group,                                      */
   int groups[2];         /*   groups,                                              */
-  int form[2];           /*   solver form (HS_FORM_SMEM or HS_FORM_SMEM1),         */
   int tuned[2];          /*   1 timed now, 0 from the cache, -1 forced             */
   double zz_mean[2];     /*   mean over realisations of the per-realisation mean   */
   double zz_std[2];      /*   of |z|^2, and its sample standard deviation          */
   double max_resid;      /* largest FP64 residual of all pairs                     */
   double seconds_setup;  /* handles, sigma, start vectors, schedule                */
-  double seconds_solve;  /* the rounds                                             */
+  double seconds_solve;  /* the launch                                             */
   double seconds_total;
 } hs_sweep_info;
 

@@ -250,45 +250,16 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem(SmemJob job0, SmemQueue q
   __shared__ int s_ok;
   const bool second = (int)blockIdx.x >= ctas0;
   const SmemQueue& q = second ? q1 : q0;
-  const int lb0 = (int)blockIdx.x - (second ? ctas0 : 0);
-  const int G = q.S, grp = lb0 / G, cta = lb0 - grp * G;
-  Slot* slots = reinterpret_cast<Slot*>(q.slots) + (size_t)grp * 2 * G;
-  T* qg0 = reinterpret_cast<T*>(q.w[0]) + (size_t)grp * q.ws_stride;
-  T* qg1 = reinterpret_cast<T*>(q.w[1]) + (size_t)grp * q.ws_stride;
-  const int b0 = q.cta_first[cta], nbk = q.cta_first[cta + 1] - b0;
-  const int rows_cap = q.rows_cap;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // layout (the same for every job of the launch): low table, block headers,
-  // 9 row arrays, reduction scratch
-  size_t off_rows = sizeof(LowEntry) * q.nlow + 128 * (size_t)nbk;
-  off_rows = (off_rows + 15) & ~size_t(15);
-  size_t off_tmp = off_rows + 9 * sizeof(T) * (size_t)rows_cap;
-  off_tmp = (off_tmp + 15) & ~size_t(15);
-  double* stmp = reinterpret_cast<double*>(smem + off_tmp);
-  unsigned gen = 0;
-  auto reduce = [&](T a, T b, double (&tot)[2]) -> bool {
-    double c0, c1;
-    cta_sum2<T>(a, b, stmp, c0, c1);
-    ++gen;
-    if (wid == 0) {
-      double t[2];
-      const bool okw = slot_reduce_w0(slots, G, cta, gen, c0, c1, t, q.limit, q.err);
-      if (lane == 0) { sbuf[0] = t[0]; sbuf[1] = t[1]; s_ok = okw; }
-    }
-    __syncthreads();
-    tot[0] = sbuf[0];
-    tot[1] = sbuf[1];
-    return s_ok != 0;
-  };
-  bool ok = true;
+  Grp2<T> c = grp2_setup<T>(q, (int)blockIdx.x - (second ? ctas0 : 0), smem, &S, &sj, sbuf, &s_ib,
+                            &s_ibp, &s_ok);
   for (int njob = 0;; ++njob) {
     // the next job: CTA 0 of the group takes it from the queue and a group
     // reduction hands the index to the other CTAs
     int jid = 0;
     if (q.jobs) {
       double tot[2];
-      const T v = (cta == 0 && threadIdx.x == 0) ? (T)atomicAdd(q.head, 1) : T(0);
-      if (!(ok = reduce(v, T(0), tot))) break;
+      const T v = (c.cta == 0 && threadIdx.x == 0) ? (T)atomicAdd(q.head, 1) : T(0);
+      if (!grp_reduce2(c, v, T(0), tot)) break;
       jid = (int)tot[0];
       if (jid >= __ldcg(q.head + 1)) break;
     } else if (njob > 0) {
@@ -296,142 +267,7 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem(SmemJob job0, SmemQueue q
     }
     if (threadIdx.x == 0) sj = q.jobs ? q.jobs[jid] : job0;
     __syncthreads();
-    const Geo& g = sj.g;
-    const T* __restrict__ bv = reinterpret_cast<const T*>(sj.b);
-    T* xout = reinterpret_cast<T*>(sj.x);
-    const double sigma = sj.sigma;
-    LowEntry* low = reinterpret_cast<LowEntry*>(smem);
-    {
-      const uint4* src = reinterpret_cast<const uint4*>(g.low);
-      uint4* dst = reinterpret_cast<uint4*>(low);
-      for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
-    }
-    uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * q.nlow);
-    {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
-      for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
-    }
-    T* QL0 = reinterpret_cast<T*>(smem + off_rows);
-    T* QL1 = QL0 + rows_cap;
-    T* P = QL0 + 2 * rows_cap;
-    T* D0 = QL0 + 3 * rows_cap;
-    T* D1 = QL0 + 4 * rows_cap;
-    T* X = QL0 + 5 * rows_cap;
-    T* MV = QL0 + 6 * rows_cap;        // M_ii
-    T* MI = QL0 + 7 * rows_cap;        // 1 / M_ii
-    T* DG = QL0 + 8 * rows_cap;        // a_ii - sigma (rebuilding it costs ~4 FP64 operations a row)
-    const uint32_t Rbase = nbk > 0 ? __ldg(&g.blocks[b0].R) : 0u;
-    __syncthreads();
-    auto each_block = [&](auto&& f) {
-      for (int lb = wid; lb < nbk; lb += NT / 32) {
-        const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
-        f(h, h.R - Rbase);
-      }
-    };
-    {
-      T acc = T(0), zm = T(0);
-      each_block([&](const Hdr& h, uint32_t l0) {
-        for (int r = lane; r < h.C; r += 32) {
-          T am;
-          const T m = row_m<T, PC>(low[h.off + r], h, am);
-          const uint32_t i = h.R + r;
-          const uint32_t l = l0 + r;
-          const T b = bv[i];
-          zm += (m == T(0)) ? T(1) : T(0);
-          const T mi = m == T(0) ? T(0) : T(1) / m;
-          const T qv = b * mi;
-          MV[l] = m; MI[l] = mi; DG[l] = am;
-          QL1[l] = qv; qg1[i] = qv;
-          QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
-          acc += qv * b;
-        }
-      });
-      double tot[2];
-      ok = reduce(acc, zm, tot);
-      if (ok && threadIdx.x == 0) {
-        init_state(S, tot[0], tot[1], sj.tol, sj.kmax, sigma);
-        s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
-        s_ibp = 1.0;                     // 1 / beta_0
-      }
-      __syncthreads();
-    }
-    while (ok && S.done != 2) {
-      const long long k = S.k;
-      const bool odd = (k & 1) != 0;
-      T* QLc = odd ? QL1 : QL0;          // q_k
-      T* QLp = odd ? QL0 : QL1;          // q_{k-1} -> q_{k+1}
-      const T* qgc = odd ? qg1 : qg0;    // q_k (global, for gathers)
-      T* qgn = odd ? qg0 : qg1;          // q_{k+1}
-      T* DA = odd ? D1 : D0;             // d_{k-2}
-      T* DB = odd ? D0 : D1;             // d_{k-3} -> d_{k-1}
-      const bool doC = S.pending != 0, doMV = S.done == 0;
-      const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
-      T acc = T(0);
-      each_block([&](const Hdr& h, uint32_t l0) {
-        if (doC)
-          for (int r = lane; r < h.C; r += 32) {
-            const uint32_t l = l0 + r;
-            const T d = cq * QLp[l] + cd1 * DA[l] + cd2 * DB[l];
-            DB[l] = d;
-            X[l] += tau * d;
-          }
-        if (doMV) {
-          T xi[JM], hx[JM];
-          block_hv_loc<T, JM>(qgc, QLc + l0, DG + l0, low, h, xi, hx);
-#pragma unroll
-          for (int j = 0; j < JM; ++j) {
-            const int r = lane + 32 * j;
-            if (j < h.J && r < h.C) {
-              P[l0 + r] = hx[j];
-              acc += xi[j] * hx[j];
-            }
-          }
-        }
-      });
-      if (!doMV) {
-        __syncthreads();
-        if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
-        __syncthreads();
-        break;
-      }
-      double tot[2];
-      if (!(ok = reduce(acc, T(0), tot))) break;
-      if (threadIdx.x == 0) {
-        S.pending = 0;
-        S.alpha = tot[0] * s_ib * s_ib;                   // q.p / beta_k^2
-        if (!isfinite(S.alpha)) { S.status = HS_NONFINITE; S.done = 2; }
-      }
-      __syncthreads();
-      if (S.done == 2) break;
-      const T c1 = (T)s_ib, c2 = (T)(S.alpha * s_ib), c3 = (T)(S.beta * s_ibp);
-      T acc2 = T(0);
-      each_block([&](const Hdr& h, uint32_t l0) {
-        for (int r = lane; r < h.C; r += 32) {
-          const uint32_t l = l0 + r;
-          const T qv = P[l] * MI[l] * c1 - c2 * QLc[l] - c3 * QLp[l];
-          QLp[l] = qv;
-          qgn[h.R + r] = qv;
-          acc2 += MV[l] * qv * qv;
-        }
-      });
-      if (!(ok = reduce(acc2, T(0), tot))) break;
-      if (threadIdx.x == 0) {
-        double ib = s_ib;
-        givens_fast(S, tot[0], ib);
-        s_ibp = s_ib;
-        s_ib = ib;
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
-    });
-    if (cta == 0 && threadIdx.x == 0) {
-      if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
-      *sj.st = S;
-    }
-    if (!ok) break;
+    if (!smem_solve2<T, PC, JM, NT>(c)) break;
   }
 }
 

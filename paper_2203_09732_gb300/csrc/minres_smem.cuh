@@ -393,6 +393,235 @@ struct SmemQueue {
   long long ws_stride;
 };
 
+// Per-CTA context of a group's solves in the two-reduction shared-memory
+// form: its queue, place in the group, reduction slots, global gather
+// vectors, shared-memory layout and the shared scalars of the solve.
+template <typename T>
+struct Grp2 {
+  const SmemQueue* q;
+  int G, cta, b0, nbk;
+  Slot* slots;
+  T* qg0;
+  T* qg1;
+  char* smem;
+  size_t off_rows;
+  double* stmp;
+  unsigned gen;
+  MinresState* S;
+  const SmemJob* sj;
+  double* sbuf;
+  double* s_ib;
+  double* s_ibp;
+  int* s_ok;
+};
+
+// Layout (the same for every job of a queue): low table, block headers of
+// the CTA, 9 row arrays, reduction scratch.
+template <typename T>
+__device__ __forceinline__ Grp2<T> grp2_setup(const SmemQueue& q, int lb, char* smem,
+                                              MinresState* S, const SmemJob* sj, double* sbuf,
+                                              double* s_ib, double* s_ibp, int* s_ok) {
+  Grp2<T> c;
+  c.q = &q;
+  c.G = q.S;
+  const int grp = lb / c.G;
+  c.cta = lb - grp * c.G;
+  c.slots = reinterpret_cast<Slot*>(q.slots) + (size_t)grp * 2 * c.G;
+  c.qg0 = reinterpret_cast<T*>(q.w[0]) + (size_t)grp * q.ws_stride;
+  c.qg1 = reinterpret_cast<T*>(q.w[1]) + (size_t)grp * q.ws_stride;
+  c.b0 = q.cta_first[c.cta];
+  c.nbk = q.cta_first[c.cta + 1] - c.b0;
+  c.smem = smem;
+  size_t off = sizeof(LowEntry) * q.nlow + 128 * (size_t)c.nbk;
+  c.off_rows = (off + 15) & ~size_t(15);
+  size_t off_tmp = c.off_rows + 9 * sizeof(T) * (size_t)q.rows_cap;
+  off_tmp = (off_tmp + 15) & ~size_t(15);
+  c.stmp = reinterpret_cast<double*>(smem + off_tmp);
+  c.gen = 0;
+  c.S = S;
+  c.sj = sj;
+  c.sbuf = sbuf;
+  c.s_ib = s_ib;
+  c.s_ibp = s_ibp;
+  c.s_ok = s_ok;
+  return c;
+}
+
+// A group reduction of two values per thread (CTA sums, then the slots);
+// totals in every thread; false when the wait gave up.
+template <typename T>
+__device__ __forceinline__ bool grp_reduce2(Grp2<T>& c, T a, T b, double (&tot)[2]) {
+  double c0, c1;
+  cta_sum2<T>(a, b, c.stmp, c0, c1);
+  ++c.gen;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (wid == 0) {
+    double t[2];
+    const bool okw = slot_reduce_w0(c.slots, c.G, c.cta, c.gen, c0, c1, t, c.q->limit, c.q->err);
+    if (lane == 0) { c.sbuf[0] = t[0]; c.sbuf[1] = t[1]; *c.s_ok = okw; }
+  }
+  __syncthreads();
+  tot[0] = c.sbuf[0];
+  tot[1] = c.sbuf[1];
+  return *c.s_ok != 0;
+}
+
+// One solve of the two-reduction shared-memory form by one CTA of a group:
+// the job in *c.sj (geometry, right-hand side, solution, state, parameters).
+// The group's CTAs call it together; it ends with x and the final state
+// written, and returns false when a wait of the group gave up (HS_TIMEOUT in
+// the state).
+template <typename T, int PC, int JM, int NT>
+__device__ __forceinline__ bool smem_solve2(Grp2<T>& c) {
+  MinresState& S = *c.S;
+  const SmemJob& sj = *c.sj;
+  double& s_ib = *c.s_ib;
+  double& s_ibp = *c.s_ibp;
+  char* smem = c.smem;
+  const int b0 = c.b0, nbk = c.nbk, cta = c.cta, rows_cap = c.q->rows_cap;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* qg0 = c.qg0;
+  T* qg1 = c.qg1;
+  auto reduce = [&](T a, T b, double (&tot)[2]) -> bool { return grp_reduce2(c, a, b, tot); };
+  bool ok = true;
+  const Geo& g = sj.g;
+  const T* __restrict__ bv = reinterpret_cast<const T*>(sj.b);
+  T* xout = reinterpret_cast<T*>(sj.x);
+  const double sigma = sj.sigma;
+  LowEntry* low = reinterpret_cast<LowEntry*>(smem);
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(g.low);
+    uint4* dst = reinterpret_cast<uint4*>(low);
+    for (int i = threadIdx.x; i < g.nlow * 2; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  uint32_t* hdrs = reinterpret_cast<uint32_t*>(smem + sizeof(LowEntry) * c.q->nlow);
+  {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(g.blocks + b0);
+    for (int i = threadIdx.x; i < nbk * 32; i += blockDim.x) hdrs[i] = __ldg(src + i);
+  }
+  T* QL0 = reinterpret_cast<T*>(smem + c.off_rows);
+  T* QL1 = QL0 + rows_cap;
+  T* P = QL0 + 2 * rows_cap;
+  T* D0 = QL0 + 3 * rows_cap;
+  T* D1 = QL0 + 4 * rows_cap;
+  T* X = QL0 + 5 * rows_cap;
+  T* MV = QL0 + 6 * rows_cap;        // M_ii
+  T* MI = QL0 + 7 * rows_cap;        // 1 / M_ii
+  T* DG = QL0 + 8 * rows_cap;        // a_ii - sigma (rebuilding it costs ~4 FP64 operations a row)
+  const uint32_t Rbase = nbk > 0 ? __ldg(&g.blocks[b0].R) : 0u;
+  __syncthreads();
+  auto each_block = [&](auto&& f) {
+    for (int lb = wid; lb < nbk; lb += NT / 32) {
+      const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+      f(h, h.R - Rbase);
+    }
+  };
+  {
+    T acc = T(0), zm = T(0);
+    each_block([&](const Hdr& h, uint32_t l0) {
+      for (int r = lane; r < h.C; r += 32) {
+        T am;
+        const T m = row_m<T, PC>(low[h.off + r], h, am);
+        const uint32_t i = h.R + r;
+        const uint32_t l = l0 + r;
+        const T b = bv[i];
+        zm += (m == T(0)) ? T(1) : T(0);
+        const T mi = m == T(0) ? T(0) : T(1) / m;
+        const T qv = b * mi;
+        MV[l] = m; MI[l] = mi; DG[l] = am;
+        QL1[l] = qv; qg1[i] = qv;
+        QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
+        acc += qv * b;
+      }
+    });
+    double tot[2];
+    ok = reduce(acc, zm, tot);
+    if (ok && threadIdx.x == 0) {
+      init_state(S, tot[0], tot[1], sj.tol, sj.kmax, sigma);
+      s_ib = S.beta > 0.0 ? 1.0 / S.beta : 0.0;
+      s_ibp = 1.0;                     // 1 / beta_0
+    }
+    __syncthreads();
+  }
+  while (ok && S.done != 2) {
+    const long long k = S.k;
+    const bool odd = (k & 1) != 0;
+    T* QLc = odd ? QL1 : QL0;          // q_k
+    T* QLp = odd ? QL0 : QL1;          // q_{k-1} -> q_{k+1}
+    const T* qgc = odd ? qg1 : qg0;    // q_k (global, for gathers)
+    T* qgn = odd ? qg0 : qg1;          // q_{k+1}
+    T* DA = odd ? D1 : D0;             // d_{k-2}
+    T* DB = odd ? D0 : D1;             // d_{k-3} -> d_{k-1}
+    const bool doC = S.pending != 0, doMV = S.done == 0;
+    const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
+    T acc = T(0);
+    each_block([&](const Hdr& h, uint32_t l0) {
+      if (doC)
+        for (int r = lane; r < h.C; r += 32) {
+          const uint32_t l = l0 + r;
+          const T d = cq * QLp[l] + cd1 * DA[l] + cd2 * DB[l];
+          DB[l] = d;
+          X[l] += tau * d;
+        }
+      if (doMV) {
+        T xi[JM], hx[JM];
+        block_hv_loc<T, JM>(qgc, QLc + l0, DG + l0, low, h, xi, hx);
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+          const int r = lane + 32 * j;
+          if (j < h.J && r < h.C) {
+            P[l0 + r] = hx[j];
+            acc += xi[j] * hx[j];
+          }
+        }
+      }
+    });
+    if (!doMV) {
+      __syncthreads();
+      if (threadIdx.x == 0) { S.pending = 0; S.done = 2; }
+      __syncthreads();
+      break;
+    }
+    double tot[2];
+    if (!(ok = reduce(acc, T(0), tot))) break;
+    if (threadIdx.x == 0) {
+      S.pending = 0;
+      S.alpha = tot[0] * s_ib * s_ib;                   // q.p / beta_k^2
+      if (!isfinite(S.alpha)) { S.status = HS_NONFINITE; S.done = 2; }
+    }
+    __syncthreads();
+    if (S.done == 2) break;
+    const T c1 = (T)s_ib, c2 = (T)(S.alpha * s_ib), c3 = (T)(S.beta * s_ibp);
+    T acc2 = T(0);
+    each_block([&](const Hdr& h, uint32_t l0) {
+      for (int r = lane; r < h.C; r += 32) {
+        const uint32_t l = l0 + r;
+        const T qv = P[l] * MI[l] * c1 - c2 * QLc[l] - c3 * QLp[l];
+        QLp[l] = qv;
+        qgn[h.R + r] = qv;
+        acc2 += MV[l] * qv * qv;
+      }
+    });
+    if (!(ok = reduce(acc2, T(0), tot))) break;
+    if (threadIdx.x == 0) {
+      double ib = s_ib;
+      givens_fast(S, tot[0], ib);
+      s_ibp = s_ib;
+      s_ib = ib;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  each_block([&](const Hdr& h, uint32_t l0) {
+    for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
+  });
+  if (cta == 0 && threadIdx.x == 0) {
+    if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
+    *sj.st = S;
+  }
+  return ok;
+}
+
 // MinresState.pad of a one-reduction solve that ended because the expansion
 // of beta_{k+1}^2 cancelled to rounding level (status HS_BREAKDOWN): the solve
 // is to be redone by the two-reduction form.

@@ -54,10 +54,10 @@ class LanczosInfo(ctypes.Structure):
 
 class SweepInfo(ctypes.Structure):
     _fields_ = [("realisations", ctypes.c_int), ("converged", ctypes.c_int),
-                ("rounds", ctypes.c_int), ("launches", ctypes.c_int), ("graph", ctypes.c_int),
-                ("nclass", ctypes.c_int), ("minres_iters", ctypes.c_longlong),
+                ("max_steps", ctypes.c_int), ("launches", ctypes.c_int), ("nclass", ctypes.c_int),
+                ("pad", ctypes.c_int), ("minres_iters", ctypes.c_longlong),
                 ("L", ctypes.c_int * 2), ("S", ctypes.c_int * 2), ("groups", ctypes.c_int * 2),
-                ("form", ctypes.c_int * 2), ("tuned", ctypes.c_int * 2),
+                ("tuned", ctypes.c_int * 2),
                 ("zz_mean", ctypes.c_double * 2), ("zz_std", ctypes.c_double * 2),
                 ("max_resid", ctypes.c_double), ("seconds_setup", ctypes.c_double),
                 ("seconds_solve", ctypes.c_double), ("seconds_total", ctypes.c_double)]
