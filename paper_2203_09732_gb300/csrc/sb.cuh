@@ -63,7 +63,7 @@ struct Sub {
   uint32_t lo;       // first row of sub-block m inside a class-wq superblock
   int32_t bdelta;    // slot-relative offset of the cut-bond (k-1, k) flip
   uint32_t meta;     // w | nmd << 8 | (m & 1) << 16 | mtop bit << 17 | valid << 24
-  uint32_t pad0;
+  float dmid_f;      // dmid rounded to FP32 (the FP32 kernels' diagonal)
   double dmid;       // Ising terms of the mid interior bonds + fields on sites k..KS-1
   int32_t md[MD_MAX];  // slot-relative offsets of the antiparallel mid interior flips
   uint32_t pad[3];
@@ -233,6 +233,7 @@ inline bool build_plan(int L, const double* h, int k, int KS, HostPlan* P, int k
       }
       for (int j = 0; j < km; ++j) d -= h[k + j] * (((m >> j) & 1) ? 0.5 : -0.5);
       b.dmid = d;
+      b.dmid_f = (float)d;
       // cut (k-1, k): flips bit k-1 of p and bit 0 of m
       if (m & 1) {  // p gains bit k-1: rank + C(k-1, w+1), in sub-block m ^ 1 (class w + 1)
         b.bdelta = (w + 1 <= k) ? -SL + (int32_t)binom64(k - 1, w + 1) : 0;

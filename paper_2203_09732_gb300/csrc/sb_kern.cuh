@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sbhv(Geo g, const T* __restrict__ 
   __shared__ double s_c[1];
   __shared__ long long s_k;
   __shared__ int s_done;
+  __shared__ float s_dts[2];   // dT - sigma of the pair's superblocks (FP32 kernels)
   double sigma = 0.0;
   if constexpr (MODE == MODE_MINRES) {
     if (threadIdx.x == 0) {
@@ -109,6 +110,10 @@ __global__ void __launch_bounds__(NT, MINB) k_sbhv(Geo g, const T* __restrict__ 
           id >= 0 ? __ldg(reinterpret_cast<const uint32_t*>(g.sup + id) + wd) : 0u;
     }
     __syncthreads();
+    // the superblocks' share of the diagonal, once per pair: FP32 kernels add
+    // it to the sub-blocks' FP32 terms (no FP64 arithmetic per sub-block)
+    if constexpr (sizeof(T) == 4)
+      if (threadIdx.x < 2) s_dts[threadIdx.x] = (float)(sh[threadIdx.x].dT - sigma);
     // phase 1: stage x into the slots (asynchronous) while the sums of the
     // whole-superblock shifts go into G
 #pragma unroll 1
@@ -150,7 +155,10 @@ __global__ void __launch_bounds__(NT, MINB) k_sbhv(Geo g, const T* __restrict__ 
       c.mbit0 = (bm >> 16) & 1u;
       c.ttop = (hm >> 17) & 1u;
       const uint32_t anti_ks = ((bm >> 17) & 1u) ^ ((hm >> 16) & 1u);
-      c.uni = (T)(__ldg(&B->dmid) + H.dT - sigma + (anti_ks ? -0.25 : 0.25));
+      if constexpr (sizeof(T) == 4)
+        c.uni = __ldg(&B->dmid_f) + s_dts[s] + (anti_ks ? -0.25f : 0.25f);
+      else
+        c.uni = __ldg(&B->dmid) + H.dT - sigma + (anti_ks ? -0.25 : 0.25);
       acc += sb_lane<T>(c, lane);
     }
   }
