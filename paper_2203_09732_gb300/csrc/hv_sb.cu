@@ -18,9 +18,12 @@ namespace sb {
 
 constexpr int NT_SB = 512;
 
+// The product kernel for a plan with km mid bits: the mid-bond count as a
+// compile-time constant for the windows the library uses (km = 4), else read
+// from the plan.
 template <typename T>
-static auto kernel_of() {
-  return k_sbhv<T, NT_SB, 2, 4, MODE_HV>;
+static auto kernel_of(int km) {
+  return km == 4 ? k_sbhv<T, NT_SB, 2, 4, MODE_HV, 3> : k_sbhv<T, NT_SB, 2, 4, MODE_HV, 0>;
 }
 
 template <typename T>
@@ -78,7 +81,7 @@ static hs_status make_dev(hs_handle* hd, int KS, DevPlan** out) {
   for (int i = 0; i <= WQ_MAX; ++i) g.nvalid[i] = P.nvalid[i];
   g.dscale = P.dscale;
   d->smem = smem_bytes<T>((int)P.low.size(), P.km);
-  auto kern = kernel_of<T>();
+  auto kern = kernel_of<T>(P.km);
   int nb = 0;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d->smem) ==
           cudaSuccess &&
@@ -283,10 +286,10 @@ hs_status launch_matvec_sb(hs_handle* hd, const void* x, void* y, hs_dtype dt, i
   if (((uintptr_t)x % es) != 0 || ((uintptr_t)y % es) != 0) return HS_OK;
   const sb::MinresArgs none{};
   if (dt == HS_F32) {
-    sb::kernel_of<float>()<<<d->grid, sb::NT_SB, d->smem, hd->stream>>>(
+    sb::kernel_of<float>(d->geo.km)<<<d->grid, sb::NT_SB, d->smem, hd->stream>>>(
         d->geo, static_cast<const float*>(x), static_cast<float*>(y), hd->d_sigma, shifted, none);
   } else {
-    sb::kernel_of<double>()<<<d->grid, sb::NT_SB, d->smem, hd->stream>>>(
+    sb::kernel_of<double>(d->geo.km)<<<d->grid, sb::NT_SB, d->smem, hd->stream>>>(
         d->geo, static_cast<const double*>(x), static_cast<double*>(y), hd->d_sigma, shifted, none);
   }
   count_launches(1);

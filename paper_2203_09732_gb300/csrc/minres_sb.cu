@@ -25,7 +25,10 @@ constexpr int NT_R = 512;   // init and pass B
 constexpr int SB_CHUNK = 8; // iterations per graph replay
 
 template <typename T>
-auto kern_A() { return sb::k_sbhv<T, NT_A, 2, 4, sb::MODE_MINRES>; }
+auto kern_A(int km) {
+  return km == 4 ? sb::k_sbhv<T, NT_A, 2, 4, sb::MODE_MINRES, 3>
+                 : sb::k_sbhv<T, NT_A, 2, 4, sb::MODE_MINRES, 0>;
+}
 // pass A on the four-low-bit layout (sb4.cuh), where its plan applies
 constexpr int NT_A4F = 512, NT_A4D = 256;
 template <typename T>
@@ -75,7 +78,7 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
   const size_t smA = use4 ? d4->smem : d->smem;
   const size_t smR = sb::rows_smem_bytes<T>(1 << g.k);
   const int gA = use4 ? grid_of(hd, kern_A4<T>(d4->geo.km), nt_a4<T>(), smA, d4->geo.npairs)
-                      : grid_of(hd, kern_A<T>(), NT_A, smA, g.npairs);
+                      : grid_of(hd, kern_A<T>(g.km), NT_A, smA, g.npairs);
   const int gI = grid_of(hd, kern_R<T, PC, sb::ROWS_INIT>(), NT_R, smR, g.npairs);
   const int gB = grid_of(hd, kern_R<T, PC, sb::ROWS_B>(), NT_R, smR, g.npairs);
   if (gA < 1 || gI < 1 || gB < 1) return HS_OK;
@@ -112,7 +115,7 @@ hs_status solve_t(hs_handle* hd, const T* b, const MinresVecs& v, double tol, lo
           kern_A4<T>(d4->geo.km)<<<gA, nt_a4<T>(), smA, cs>>>(d4->geo, nullptr, nullptr,
                                                               hd->d_sigma, 1, mA);
         else
-          kern_A<T>()<<<gA, NT_A, smA, cs>>>(g, nullptr, nullptr, hd->d_sigma, 1, mA);
+          kern_A<T>(g.km)<<<gA, NT_A, smA, cs>>>(g, nullptr, nullptr, hd->d_sigma, 1, mA);
         kern_R<T, PC, sb::ROWS_B>()<<<gB, NT_R, smR, cs>>>(g, nullptr, mB, 0.0, 0, hd->d_sigma);
       }
       e = cudaStreamEndCapture(cs, &graph);

@@ -413,7 +413,17 @@ struct Lane {
 // memory only, then one coalesced store. A lane past the last row repeats row
 // C - 1 and does not store. Returns the lane's sum of x_i y_i over its rows
 // (alpha_k of Algorithm 2 when x = q_k).
-template <typename T>
+// Byte q & 3 of wd, zero-extended (one byte permute on the device).
+__host__ __device__ __forceinline__ uint32_t sb_byte(uint32_t wd, int q) {
+#ifdef __CUDA_ARCH__
+  return __byte_perm(wd, 0u, 0x4440u | (uint32_t)(q & 3));
+#else
+  return (wd >> (8 * (q & 3))) & 0xFFu;
+#endif
+}
+
+// NMID > 0: the number of mid bonds (km - 1) known at compile time.
+template <typename T, int NMID = 0>
 __host__ __device__ __forceinline__ T sb_lane(const Lane<T>& c, int lane) {
   const int J = (c.C + 31) >> 5;
   T dot = T(0);
@@ -429,11 +439,16 @@ __host__ __device__ __forceinline__ T sb_lane(const Lane<T>& c, int lane) {
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const uint32_t wd = q < 4 ? e.nb0 : (q < 8 ? e.nb1 : e.meta);
-      a += c.tl[(wd >> (8 * (q & 3))) & 0xFFu];
+      a += c.tl[sb_byte(wd, q)];
     }
+    if constexpr (NMID > 0) {
 #pragma unroll
-    for (int q = 0; q < MD_MAX; ++q)
-      if (q < c.nmid) a += c.tl[r + c.md[q]];
+      for (int q = 0; q < NMID; ++q) a += c.tl[r + c.md[q]];
+    } else {
+#pragma unroll
+      for (int q = 0; q < MD_MAX; ++q)
+        if (q < c.nmid) a += c.tl[r + c.md[q]];
+    }
     const uint32_t code = (e.meta >> 20) & 3u;
     const uint32_t x0 = (code & 1u) ^ c.mbit0;
     const uint32_t x1 = (code >> 1) ^ c.ttop;

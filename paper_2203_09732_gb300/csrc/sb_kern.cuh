@@ -48,7 +48,7 @@ struct MinresArgs {
 constexpr int MODE_HV = 0;       // plain product
 constexpr int MODE_MINRES = 1;   // MINRES pass A
 
-template <typename T, int NT, int MINB, int U, int MODE>
+template <typename T, int NT, int MINB, int U, int MODE, int NMID = 0>
 __global__ void __launch_bounds__(NT, MINB) k_sbhv(Geo g, const T* __restrict__ x,
                                                    T* __restrict__ y, const double* d_sigma,
                                                    int shifted, MinresArgs ma) {
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(NT, MINB) k_sbhv(Geo g, const T* __restrict__ 
         c.uni = __ldg(&B->dmid_f) + s_dts[s] + (anti_ks ? -0.25f : 0.25f);
       else
         c.uni = __ldg(&B->dmid) + H.dT - sigma + (anti_ks ? -0.25 : 0.25);
-      acc += sb_lane<T>(c, lane);
+      acc += sb_lane<T, NMID>(c, lane);
     }
   }
   if constexpr (MODE == MODE_MINRES) {
