@@ -409,10 +409,6 @@ struct Lane {
   T uni;                 // dmid + dT - sigma +- 1/4 for bond (KS-1, KS)
 };
 
-// Phase 2: the rows of one sub-block for one lane (r = lane + 32 j); shared
-// memory only, then one coalesced store. A lane past the last row repeats row
-// C - 1 and does not store. Returns the lane's sum of x_i y_i over its rows
-// (alpha_k of Algorithm 2 when x = q_k).
 // Byte q & 3 of wd, zero-extended (one byte permute on the device).
 __host__ __device__ __forceinline__ uint32_t sb_byte(uint32_t wd, int q) {
 #ifdef __CUDA_ARCH__
@@ -422,7 +418,11 @@ __host__ __device__ __forceinline__ uint32_t sb_byte(uint32_t wd, int q) {
 #endif
 }
 
-// NMID > 0: the number of mid bonds (km - 1) known at compile time.
+// Phase 2: the rows of one sub-block for one lane (r = lane + 32 j); shared
+// memory only, then one coalesced store. A lane past the last row repeats row
+// C - 1 and does not store. Returns the lane's sum of x_i y_i over its rows
+// (alpha_k of Algorithm 2 when x = q_k). NMID > 0: the number of mid bonds
+// (km - 1) known at compile time.
 template <typename T, int NMID = 0>
 __host__ __device__ __forceinline__ T sb_lane(const Lane<T>& c, int lane) {
   const int J = (c.C + 31) >> 5;
