@@ -203,8 +203,9 @@ hs_status launch_unrank(hs_handle* hd, long long first, long long count, unsigne
 hs_status launch_rank(hs_handle* hd, const unsigned int* st, long long count, long long* out);
 hs_status launch_diag(hs_handle* hd, double* diag, hs_precond pc, double* minv);
 // FP64 r = b - (H - sigma) x; returns sum r^2/M and sum r^2 and the same for b.
+// x_zero: x is zero (r = b; x is not read).
 hs_status resid64(hs_handle* hd, const double* b, const double* x, double* r, hs_precond pc,
-                  double sums_out[4]);
+                  double sums_out[4], bool x_zero = false);
 
 // minres_sb.cu: destroy the cached superblock MINRES graphs of precision ti
 // (0 FP32, 1 FP64), e.g. before the workspace they point into is freed

@@ -95,7 +95,11 @@ __global__ void __launch_bounds__(HV_THREADS) k_diag(Geo g, double* diag, double
 // ---------------------------------------------------------------------------
 // FP64 residual r = b - (H - sigma) x with per-CTA partial sums
 // [sum r^2 / M, sum r^2, sum b^2 / M, sum b^2] (host adds them in order).
-template <int PC>
+// MODE: RES_PRODUCT forms the product here; RES_ZERO: x is zero (the first
+// refinement sweep), so r = b and x is not read; RES_GIVEN: rv already holds
+// (H - sigma) x (from a faster product kernel) and is overwritten in place.
+constexpr int RES_PRODUCT = 0, RES_ZERO = 1, RES_GIVEN = 2;
+template <int PC, int MODE>
 __global__ void __launch_bounds__(HV_THREADS) k_resid64(Geo g, const double* __restrict__ bv,
                                                         const double* __restrict__ x,
                                                         double* __restrict__ rv,
@@ -108,7 +112,12 @@ __global__ void __launch_bounds__(HV_THREADS) k_resid64(Geo g, const double* __r
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for_blocks(g, sigma, [&](const Hdr& h) {
     double xi[JMAX], hx[JMAX];
-    block_hv<double>(x, s, h, xi, hx);
+    if constexpr (MODE == RES_PRODUCT) {
+      block_hv<double>(x, s, h, xi, hx);
+    } else {
+#pragma unroll
+      for (int j = 0; j < JMAX; ++j) hx[j] = 0.0;
+    }
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
       const int r = lane + 32 * j;
@@ -118,7 +127,7 @@ __global__ void __launch_bounds__(HV_THREADS) k_resid64(Geo g, const double* __r
         const double m = precond_t<PC, double>(diag_d(e, h, xc), naf_row(e.packed, h, xc));
         const uint32_t i = h.R + r;
         const double bi_ = bv[i];
-        const double ri = bi_ - hx[j];
+        const double ri = bi_ - (MODE == RES_GIVEN ? rv[i] : hx[j]);
         rv[i] = ri;
         acc[0] += ri * ri / m;
         acc[1] += ri * ri;
@@ -203,28 +212,47 @@ hs_status launch_diag(hs_handle* hd, double* diag, hs_precond pc, double* minv) 
   return HS_OK;
 }
 
+template <int MODE>
+static hs_status resid64_t(hs_handle* hd, const double* b, const double* x, double* r,
+                           hs_precond pc, int grid, size_t sm) {
+  const Geo g = hd->geo();
+  switch (pc) {
+    case HS_PC_ID:
+      if (prep_smem(hd, k_resid64<0, MODE>, sm) != HS_OK) return HS_CUDA;
+      k_resid64<0, MODE><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
+      break;
+    case HS_PC_JACOBI:
+      if (prep_smem(hd, k_resid64<1, MODE>, sm) != HS_OK) return HS_CUDA;
+      k_resid64<1, MODE><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
+      break;
+    default:
+      if (prep_smem(hd, k_resid64<2, MODE>, sm) != HS_OK) return HS_CUDA;
+      k_resid64<2, MODE><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
+      break;
+  }
+  HS_CUDA_TRY(hd, cudaGetLastError());
+  return HS_OK;
+}
+
 hs_status resid64(hs_handle* hd, const double* b, const double* x, double* r, hs_precond pc,
-                  double sums_out[4]) {
+                  double sums_out[4], bool x_zero) {
   hs_status st = ensure_reduce(hd);
   if (st != HS_OK) return st;
   const size_t sm = smem_of<double>(hd);
   const int grid = row_grid(hd);
-  const Geo g = hd->geo();
-  switch (pc) {
-    case HS_PC_ID:
-      if (prep_smem(hd, k_resid64<0>, sm) != HS_OK) return HS_CUDA;
-      k_resid64<0><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
-      break;
-    case HS_PC_JACOBI:
-      if (prep_smem(hd, k_resid64<1>, sm) != HS_OK) return HS_CUDA;
-      k_resid64<1><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
-      break;
-    default:
-      if (prep_smem(hd, k_resid64<2>, sm) != HS_OK) return HS_CUDA;
-      k_resid64<2><<<grid, HV_THREADS, sm, hd->stream>>>(g, b, x, r, hd->d_sigma, hd->d_partial); count_launches(1);
-      break;
+  if (x_zero) {
+    st = resid64_t<RES_ZERO>(hd, b, x, r, pc, grid, sm);
+  } else {
+    // where a superblock FP64 product applies (L >= 24) it is faster than the
+    // block form's: form (H - sigma) x in r, then r = b - r with the sums
+    const char* e = getenv("HS_HV_SB");
+    bool used = false;
+    if (e ? e[0] == '1' : hd->L >= 24)
+      if ((st = launch_matvec_sb(hd, x, r, HS_F64, 1, &used)) != HS_OK) return st;
+    st = used ? resid64_t<RES_GIVEN>(hd, b, x, r, pc, grid, sm)
+              : resid64_t<RES_PRODUCT>(hd, b, x, r, pc, grid, sm);
   }
-  HS_CUDA_TRY(hd, cudaGetLastError());
+  if (st != HS_OK) return st;
   return sum_partials(hd, grid, 4, sums_out);
 }
 

@@ -810,7 +810,8 @@ hs_status minres_mixed(hs_handle* hd, const double* b, double* x, double tol, lo
   hs_status out = HS_NOT_CONVERGED;
   int sweeps = 0;
   for (int sweep = 0; sweep < 64; ++sweep) {
-    if ((st = resid64(hd, b, x, r, pc, sums)) != HS_OK) return st;
+    // x = 0 before the first sweep: r = b without a product
+    if ((st = resid64(hd, b, x, r, pc, sums, sweep == 0)) != HS_OK) return st;
     const double bM = std::sqrt(sums[2]), rM = std::sqrt(sums[0]);
     const double rel = bM > 0 ? rM / bM : 0.0;
     if (info) {

@@ -176,3 +176,31 @@ def test_matches_persistent_form_l24(dtype, monkeypatch):
     scale = np.abs(xs["0"]).max()
     tol = 1e-12 if dtype == "f64" else 1e-4
     assert np.abs(xs["1"] - xs["0"]).max() <= tol * scale
+
+
+@pytest.mark.parametrize("L", [14, 16])
+def test_refinement_residual_through_superblock_product(L, small_sb, monkeypatch):
+    """The FP64 residual b - (H - sigma) x of the refinement, with the product
+    taken by the superblock FP64 kernel (HS_HV_SB=1; the default from L = 24):
+    the M^-1- and 2-norm residuals that hs_minres reports after an FP64 solve
+    capped at 20 iterations, and after an FP32 + refinement solve, against the
+    oracle's explicit A applied to the returned x."""
+    hs = need_gpu()
+    monkeypatch.setenv("HS_HV_SB", "1")
+    hv = inputs.disorder(L, 3.0, 2)
+    H, diag, st = hamiltonian.build(L, hv)
+    sigma = 0.05
+    A = (H - sigma * sp.identity(H.shape[0])).tocsr()
+    b = inputs.gaussian(A.shape[0], 5)
+    M = hamiltonian.precond_diag(H, diag, sigma, "row")
+    with hs.Chain(L, hv, sigma=sigma) as c:
+        x, info = c.minres(to_dev(b), tol=0.0, kmax=20, precond="row", allow_not_converged=True)
+        xm, im = c.minres(to_dev(b), tol=1e-10, precond="row", mixed=True, inner_tol=1e-4)
+    for xx, inf in ((x, info), (xm, im)):
+        r = b - A @ xx.cpu().numpy()
+        rel_m = np.sqrt(r @ (r / M)) / np.sqrt(b @ (b / M))
+        rel_2 = np.linalg.norm(r) / np.linalg.norm(b)
+        # FP64 rounding of b - A x is ~1e-15 of |b| (absolute floor 1e-13)
+        assert abs(inf["resid_minv"] - rel_m) <= 1e-9 * rel_m + 1e-13
+        assert abs(inf["resid_2"] - rel_2) <= 1e-9 * rel_2 + 1e-13
+    assert im["resid_minv"] <= 1e-10 and im["sweeps"] >= 2
