@@ -48,10 +48,11 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
 
 // Rows of one block whose own segment (self and low-interior neighbours) is
 // read from shared memory xl; the other gathers come from global xg.
+// The rows are lane + 32 (j0 + j), j < JM: the block's 32-row chunks j0 on.
 template <typename T, int JM>
 __device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* xl, const T* dg,
                                              const LowEntry* low, const Hdr& h, T (&xi)[JM],
-                                             T (&hx)[JM]) {
+                                             T (&hx)[JM], int j0 = 0) {
   const int lane = threadIdx.x & 31;
   const T* xb = xg + h.R;
   T side[JM];
@@ -60,8 +61,8 @@ __device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* 
     xi[j] = T(0);
     side[j] = T(0);
     hx[j] = T(0);
-    const int r = lane + 32 * j;
-    if (j < h.J && r < h.C) {
+    const int r = lane + 32 * (j0 + j);
+    if (j0 + j < h.J && r < h.C) {
       const LowEntry& e = low[h.off + r];
       const uint32_t xc = cut_mask(e.packed, h);
       xi[j] = xl[r];
@@ -76,10 +77,11 @@ __device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* 
 #pragma unroll
     for (int mm = 0; mm < HG; ++mm) {
       const bool on = m0 + mm < h.nh;
-      const T* xh = xb + (on ? hdr_hd(h, m0 + mm) : 0) + lane;
+      const T* xh = xb + (on ? hdr_hd(h, m0 + mm) : 0) + lane + 32 * j0;
 #pragma unroll
       for (int j = 0; j < JM; ++j)
-        v[mm][j] = (on && j < h.J && lane + 32 * j < h.C) ? ldx<T, true>(xh + 32 * j) : T(0);
+        v[mm][j] = (on && j0 + j < h.J && lane + 32 * (j0 + j) < h.C) ? ldx<T, true>(xh + 32 * j)
+                                                                      : T(0);
     }
     // only the bonds that exist: the count is the same for the whole warp, so
     // this skips FP64 adds of zero (the FP64 pipe bounds this pass)
@@ -91,8 +93,8 @@ __device__ __forceinline__ void block_hv_loc(const T* __restrict__ xg, const T* 
   }
 #pragma unroll
   for (int j = 0; j < JM; ++j) {
-    const int r = lane + 32 * j;
-    if (j < h.J && r < h.C) {
+    const int r = lane + 32 * (j0 + j);
+    if (j0 + j < h.J && r < h.C) {
       const LowEntry& e = low[h.off + r];
       const uint32_t pk = e.packed;
       T acc = hx[j] + side[j];
@@ -510,16 +512,61 @@ __device__ __forceinline__ bool smem_solve2(Grp2<T>& c) {
   T* DG = QL0 + 8 * rows_cap;        // a_ii - sigma (rebuilding it costs ~4 FP64 operations a row)
   const uint32_t Rbase = nbk > 0 ? __ldg(&g.blocks[b0].R) : 0u;
   __syncthreads();
-  auto each_block = [&](auto&& f) {
-    for (int lb = wid; lb < nbk; lb += NT / 32) {
+  // Work of a pass, f(h, l0, j0, nj): chunks j0 .. j0 + nj - 1 (32 rows each)
+  // of one block. Either whole blocks dealt round-robin to the warps, or, in
+  // FP64 where that leaves the slowest warp with more chunks, single chunks
+  // dealt round-robin in block order (the same choice in every pass of the
+  // solve). Measured on 152 SMs (two-reduction form, us per iteration): FP64
+  // L = 16 21.8 -> 19.6, L = 20 41.2 -> 38.1; FP32 slower by chunks (L = 20:
+  // 19.9 -> 35.5), so FP32 keeps whole blocks.
+  constexpr int NW = NT / 32;
+  auto block_chunks = [&](int lb) {
+    return (g.cls_C[hdrs[lb * 32 + 3] & 0xFFu] + 31) >> 5;   // word 3: w | ...
+  };
+  bool by_chunk = false;
+  if constexpr (sizeof(T) == 8) {
+    int tot = 0, worst = 0;
+    for (int w = 0; w < NW; ++w) {
+      int mine = 0;
+      for (int lb = w; lb < nbk; lb += NW) mine += block_chunks(lb);
+      worst = max(worst, mine);
+      tot += mine;
+    }
+    by_chunk = (tot + NW - 1) / NW < worst;
+  }
+  auto each_part = [&](auto&& f) {
+    if constexpr (sizeof(T) == 8) {
+      if (by_chunk) {
+        int t = 0;                               // chunks before block lb
+        for (int lb = 0; lb < nbk; ++lb) {
+          const int J = block_chunks(lb);
+          int jc = (wid - t) % NW;
+          if (jc < 0) jc += NW;
+          if (jc < J) {
+            const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+            for (; jc < J; jc += NW) f(h, h.R - Rbase, jc, 1);
+          }
+          t += J;
+        }
+        return;
+      }
+    }
+    for (int lb = wid; lb < nbk; lb += NW) {
       const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
-      f(h, h.R - Rbase);
+      f(h, h.R - Rbase, 0, h.J);
+    }
+  };
+  // the rows of a part, one per lane and chunk
+  auto each_row = [&](const Hdr& h, int j0, int nj, auto&& g_row) {
+    for (int j = j0; j < j0 + nj; ++j) {
+      const int r = lane + 32 * j;
+      if (r < h.C) g_row(r);
     }
   };
   {
     T acc = T(0), zm = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) {
+    each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
+      each_row(h, j0, nj, [&](int r) {
         T am;
         const T m = row_m<T, PC>(low[h.off + r], h, am);
         const uint32_t i = h.R + r;
@@ -532,7 +579,7 @@ __device__ __forceinline__ bool smem_solve2(Grp2<T>& c) {
         QL1[l] = qv; qg1[i] = qv;
         QL0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
         acc += qv * b;
-      }
+      });
     });
     double tot[2];
     ok = reduce(acc, zm, tot);
@@ -555,23 +602,33 @@ __device__ __forceinline__ bool smem_solve2(Grp2<T>& c) {
     const bool doC = S.pending != 0, doMV = S.done == 0;
     const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
     T acc = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
+    each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
       if (doC)
-        for (int r = lane; r < h.C; r += 32) {
+        each_row(h, j0, nj, [&](int r) {
           const uint32_t l = l0 + r;
           const T d = cq * QLp[l] + cd1 * DA[l] + cd2 * DB[l];
           DB[l] = d;
           X[l] += tau * d;
-        }
+        });
       if (doMV) {
-        T xi[JM], hx[JM];
-        block_hv_loc<T, JM>(qgc, QLc + l0, DG + l0, low, h, xi, hx);
+        if (sizeof(T) == 8 && by_chunk) {  // one chunk
+          T xi[1], hx[1];
+          block_hv_loc<T, 1>(qgc, QLc + l0, DG + l0, low, h, xi, hx, j0);
+          const int r = lane + 32 * j0;
+          if (r < h.C) {
+            P[l0 + r] = hx[0];
+            acc += xi[0] * hx[0];
+          }
+        } else {                         // a whole block
+          T xi[JM], hx[JM];
+          block_hv_loc<T, JM>(qgc, QLc + l0, DG + l0, low, h, xi, hx);
 #pragma unroll
-        for (int j = 0; j < JM; ++j) {
-          const int r = lane + 32 * j;
-          if (j < h.J && r < h.C) {
-            P[l0 + r] = hx[j];
-            acc += xi[j] * hx[j];
+          for (int j = 0; j < JM; ++j) {
+            const int r = lane + 32 * j;
+            if (j < h.J && r < h.C) {
+              P[l0 + r] = hx[j];
+              acc += xi[j] * hx[j];
+            }
           }
         }
       }
@@ -593,14 +650,14 @@ __device__ __forceinline__ bool smem_solve2(Grp2<T>& c) {
     if (S.done == 2) break;
     const T c1 = (T)s_ib, c2 = (T)(S.alpha * s_ib), c3 = (T)(S.beta * s_ibp);
     T acc2 = T(0);
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) {
+    each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
+      each_row(h, j0, nj, [&](int r) {
         const uint32_t l = l0 + r;
         const T qv = P[l] * MI[l] * c1 - c2 * QLc[l] - c3 * QLp[l];
         QLp[l] = qv;
         qgn[h.R + r] = qv;
         acc2 += MV[l] * qv * qv;
-      }
+      });
     });
     if (!(ok = reduce(acc2, T(0), tot))) break;
     if (threadIdx.x == 0) {
@@ -612,8 +669,8 @@ __device__ __forceinline__ bool smem_solve2(Grp2<T>& c) {
     __syncthreads();
   }
   __syncthreads();
-  each_block([&](const Hdr& h, uint32_t l0) {
-    for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
+  each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
+    each_row(h, j0, nj, [&](int r) { xout[h.R + r] = X[l0 + r]; });
   });
   if (cta == 0 && threadIdx.x == 0) {
     if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
