@@ -48,12 +48,12 @@ constexpr int PIPE_NV = 5;           // S1..S5 (S6 is carried)
 template <typename T>
 constexpr double EXPANSION_FLOOR = sizeof(T) == 8 ? 1e-8 : 1e-3;
 
-// Shared memory: low table, block headers, 11 row arrays, reduction staging.
+// Shared memory: low table, block headers, 12 row arrays, reduction staging.
 template <typename T>
 size_t smr1_bytes(int nlow, int hdr_cap, int rows_cap, int nt) {
   size_t b = sizeof(LowEntry) * (size_t)nlow + 128 * (size_t)hdr_cap;
   b = (b + 15) & ~size_t(15);
-  b += 11 * sizeof(T) * (size_t)rows_cap;
+  b += 12 * sizeof(T) * (size_t)rows_cap;
   b = (b + 15) & ~size_t(15);
   return b + sizeof(double) * PIPE_NV * (sizeof(T) == 8 ? (size_t)nt : 32);
 }
@@ -80,12 +80,12 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue 
   const int b0 = q.cta_first[cta], nbk = q.cta_first[cta + 1] - b0;
   const int rows_cap = q.rows_cap;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nact = min(nbk, NT / 32);         // warps that own blocks
+  int nact = min(nbk, NT / 32);               // warps that hold rows (set per job below)
   // layout (the same for every job of the launch): low table, block headers,
-  // 11 row arrays, reduction staging
+  // 12 row arrays, reduction staging
   size_t off_rows = sizeof(LowEntry) * q.nlow + 128 * (size_t)nbk;
   off_rows = (off_rows + 15) & ~size_t(15);
-  size_t off_tmp = off_rows + 11 * sizeof(T) * (size_t)rows_cap;
+  size_t off_tmp = off_rows + 12 * sizeof(T) * (size_t)rows_cap;
   off_tmp = (off_tmp + 15) & ~size_t(15);
   double* stmp = reinterpret_cast<double*>(smem + off_tmp);
   LowEntry* low = reinterpret_cast<LowEntry*>(smem);
@@ -96,11 +96,12 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue 
   T* P1 = Q0 + 3 * rows_cap;
   T* D0 = Q0 + 4 * rows_cap;                  // d_j in D[j & 1]
   T* D1 = Q0 + 5 * rows_cap;
-  T* VL = Q0 + 6 * rows_cap;                  // v_k (own rows)
-  T* X = Q0 + 7 * rows_cap;
-  T* MV = Q0 + 8 * rows_cap;                  // M_ii
-  T* MI = Q0 + 9 * rows_cap;                  // 1 / M_ii
-  T* DG = Q0 + 10 * rows_cap;                 // a_ii - sigma
+  T* V0 = Q0 + 6 * rows_cap;                  // v_j (own rows) in V[j & 1]
+  T* V1 = Q0 + 7 * rows_cap;
+  T* X = Q0 + 8 * rows_cap;
+  T* MV = Q0 + 9 * rows_cap;                  // M_ii
+  T* MI = Q0 + 10 * rows_cap;                 // 1 / M_ii
+  T* DG = Q0 + 11 * rows_cap;                 // a_ii - sigma
   unsigned gen = 0;
   auto reduce = [&](const T (&a)[PIPE_NV]) -> bool {
     cta_sumN<T, PIPE_NV>(a, nact, stmp, s_cta);
@@ -165,18 +166,82 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue 
     }
     const uint32_t Rbase = nbk > 0 ? __ldg(&g.blocks[b0].R) : 0u;
     __syncthreads();
-    auto each_block = [&](auto&& f) {
-      for (int lb = wid; lb < nbk; lb += NT / 32) {
-        const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
-        f(h, h.R - Rbase);
+    // Work of a pass, f(h, l0, j0, nj): chunks j0 .. j0 + nj - 1 (32 rows
+    // each) of one block: whole blocks dealt round-robin to the warps, or, in
+    // FP64 where that leaves the slowest warp with more chunks, single chunks
+    // dealt round-robin in block order (as in smem_solve2). Each pass reads
+    // v_k and writes v_{k+1} in different arrays, so chunks of one block may
+    // run on different warps.
+    constexpr int NW = NT / 32;
+    auto block_chunks = [&](int lb) {
+      return (g.cls_C[hdrs[lb * 32 + 3] & 0xFFu] + 31) >> 5;
+    };
+    bool by_chunk = false;
+    nact = min(nbk, NW);
+    if constexpr (sizeof(T) == 8) {
+      int tot = 0, worst = 0;
+      for (int w = 0; w < NW; ++w) {
+        int mine = 0;
+        for (int lb = w; lb < nbk; lb += NW) mine += block_chunks(lb);
+        worst = max(worst, mine);
+        tot += mine;
       }
+      by_chunk = (tot + NW - 1) / NW < worst;
+      if (by_chunk) nact = min(tot, NW);
+    }
+    auto each_part = [&](auto&& f) {
+      if constexpr (sizeof(T) == 8) {
+        if (by_chunk) {
+          int t = 0;
+          for (int lb = 0; lb < nbk; ++lb) {
+            const int J = block_chunks(lb);
+            int jc = (wid - t) % NW;
+            if (jc < 0) jc += NW;
+            if (jc < J) {
+              const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+              for (; jc < J; jc += NW) f(h, h.R - Rbase, jc, 1);
+            }
+            t += J;
+          }
+          return;
+        }
+      }
+      for (int lb = wid; lb < nbk; lb += NW) {
+        const Hdr h = make_hdr(g, hdrs[lb * 32 + lane], sigma);
+        f(h, h.R - Rbase, 0, h.J);
+      }
+    };
+    auto each_row = [&](const Hdr& h, int j0, int nj, auto&& g_row) {
+      for (int j = j0; j < j0 + nj; ++j) {
+        const int r = lane + 32 * j;
+        if (r < h.C) g_row(r);
+      }
+    };
+    // the product of a part's rows, then upd(r, x_r, ((H - sigma) x)_r) per row
+    auto part_hv = [&](const T* xgl, const T* xloc, const Hdr& h, uint32_t l0, int j0, int nj,
+                       auto&& upd) {
+      if (sizeof(T) == 8 && by_chunk) {
+        T xi[1], hx[1];
+        block_hv_loc<T, 1>(xgl, xloc + l0, DG + l0, low, h, xi, hx, j0);
+        const int r = lane + 32 * j0;
+        if (r < h.C) upd(r, xi[0], hx[0]);
+      } else {
+        T xi[JM], hx[JM];
+        block_hv_loc<T, JM>(xgl, xloc + l0, DG + l0, low, h, xi, hx);
+#pragma unroll
+        for (int j = 0; j < JM; ++j) {
+          const int r = lane + 32 * j;
+          if (j < h.J && r < h.C) upd(r, xi[j], hx[j]);
+        }
+      }
+      (void)nj;
     };
     // q_1 = M^-1 b (x_0 = 0), q_0 = p_0 = 0, d_0 = d_{-1} = 0; q_1 is published
     // for the first product
     {
       T a[PIPE_NV] = {};
-      each_block([&](const Hdr& h, uint32_t l0) {
-        for (int r = lane; r < h.C; r += 32) {
+      each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
+        each_row(h, j0, nj, [&](int r) {
           T am;
           const T m = row_m<T, PC>(low[h.off + r], h, am);
           const uint32_t i = h.R + r;
@@ -189,7 +254,7 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue 
           Q1[l] = q; qg[i] = q;
           Q0[l] = T(0); P0[l] = T(0); D0[l] = T(0); D1[l] = T(0); X[l] = T(0);
           a[0] += q * b;
-        }
+        });
       });
       ok = reduce(a);
       if (ok && threadIdx.x == 0) {
@@ -202,22 +267,16 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue 
     // p_1 = (H - sigma) q_1, v_1 and the sums of step 1 (S3 = S5 = S6 = 0)
     if (ok && S.done == 0) {
       T a[PIPE_NV] = {};
-      each_block([&](const Hdr& h, uint32_t l0) {
-        T xi[JM], hx[JM];
-        block_hv_loc<T, JM>(qg, Q1 + l0, DG + l0, low, h, xi, hx);
-  #pragma unroll
-        for (int j = 0; j < JM; ++j) {
-          const int r = lane + 32 * j;
-          if (j < h.J && r < h.C) {
-            const uint32_t l = l0 + r;
-            const T p = hx[j];
-            const T v = MI[l] * p;
-            P1[l] = p; VL[l] = v; vg1[h.R + r] = v;
-            a[0] += xi[j] * p;
-            a[1] += p * v;
-            a[3] += MV[l] * xi[j] * xi[j];
-          }
-        }
+      each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
+        part_hv(qg, Q1, h, l0, j0, nj, [&](int r, T xv, T hv) {
+          const uint32_t l = l0 + r;
+          const T p = hv;
+          const T v = MI[l] * p;
+          P1[l] = p; V1[l] = v; vg1[h.R + r] = v;
+          a[0] += xv * p;
+          a[1] += p * v;
+          a[3] += MV[l] * xv * xv;
+        });
       });
       ok = reduce(a);
       if (threadIdx.x == 0) s_sum[PIPE_NV] = 0.0;
@@ -265,44 +324,39 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue 
       T* Dk = odd ? D1 : D0;                      // d_{k-2} -> d_k
       const T* vgk = odd ? vg1 : vg0;             // v_k
       T* vgn = odd ? vg0 : vg1;                   // v_{k+1}
+      const T* Vk = odd ? V1 : V0;                // v_k (own rows)
+      T* Vn = odd ? V0 : V1;                      // v_{k+1}
       const T cq = (T)S.cq, cd1 = (T)S.cd1, cd2 = (T)S.cd2, tau = (T)S.tau;
       const T c1 = (T)s_c[0], c2 = (T)s_c[1], c3 = (T)s_c[2];
       T a[PIPE_NV] = {};
-      each_block([&](const Hdr& h, uint32_t l0) {
+      each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
         // d_k = (q_k / beta_k - delta_k d_{k-1} - eps_k d_{k-2}) / gamma_k, x_k
-        for (int r = lane; r < h.C; r += 32) {
+        each_row(h, j0, nj, [&](int r) {
           const uint32_t l = l0 + r;
           const T d = cq * Qk[l] + cd1 * Dm[l] + cd2 * Dk[l];
           Dk[l] = d;
           X[l] += tau * d;
-        }
+        });
         if (!doMV) return;
         if (repl) {
-          for (int r = lane; r < h.C; r += 32) {
+          each_row(h, j0, nj, [&](int r) {
             const uint32_t l = l0 + r;
-            const T q = c1 * VL[l] - c2 * Qk[l] - c3 * Qm[l];
+            const T q = c1 * Vk[l] - c2 * Qk[l] - c3 * Qm[l];
             Qm[l] = q;
             qg[h.R + r] = q;
-          }
+          });
           return;
         }
-        T xi[JM], hx[JM];
-        block_hv_loc<T, JM>(vgk, VL + l0, DG + l0, low, h, xi, hx);   // xi = v_k
-        __syncwarp();                             // the block's reads of VL are done
-  #pragma unroll
-        for (int j = 0; j < JM; ++j) {
-          const int r = lane + 32 * j;
-          if (j < h.J && r < h.C) {
-            const uint32_t l = l0 + r;
-            const T qo = Qk[l];
-            const T q = c1 * xi[j] - c2 * qo - c3 * Qm[l];
-            const T p = c1 * hx[j] - c2 * Pk[l] - c3 * Pm[l];
-            const T v = MI[l] * p;
-            Qm[l] = q; Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
-            const T mq = MV[l] * q;
-            a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
-          }
-        }
+        part_hv(vgk, Vk, h, l0, j0, nj, [&](int r, T xv, T hv) {   // xv = v_k
+          const uint32_t l = l0 + r;
+          const T qo = Qk[l];
+          const T q = c1 * xv - c2 * qo - c3 * Qm[l];
+          const T p = c1 * hv - c2 * Pk[l] - c3 * Pm[l];
+          const T v = MI[l] * p;
+          Qm[l] = q; Pm[l] = p; Vn[l] = v; vgn[h.R + r] = v;
+          const T mq = MV[l] * q;
+          a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
+        });
       });
       if (!doMV) {                                // the last d/x update only
         __syncthreads();
@@ -313,30 +367,24 @@ __global__ void __launch_bounds__(NT, 1) k_minres_smem1(SmemJob job0, SmemQueue 
       if (repl) {
         // publish q_{k+1}, then p_{k+1} = (H - sigma) q_{k+1}
         if (!(ok = reduce(a))) break;
-        each_block([&](const Hdr& h, uint32_t l0) {
-          T xi[JM], hx[JM];
-          block_hv_loc<T, JM>(qg, Qm + l0, DG + l0, low, h, xi, hx);  // xi = q_{k+1}
-  #pragma unroll
-          for (int j = 0; j < JM; ++j) {
-            const int r = lane + 32 * j;
-            if (j < h.J && r < h.C) {
-              const uint32_t l = l0 + r;
-              const T qo = Qk[l];
-              const T q = xi[j];
-              const T p = hx[j];
-              const T v = MI[l] * p;
-              Pm[l] = p; VL[l] = v; vgn[h.R + r] = v;
-              const T mq = MV[l] * q;
-              a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
-            }
-          }
+        each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
+          part_hv(qg, Qm, h, l0, j0, nj, [&](int r, T xv, T hv) {   // xv = q_{k+1}
+            const uint32_t l = l0 + r;
+            const T qo = Qk[l];
+            const T q = xv;
+            const T p = hv;
+            const T v = MI[l] * p;
+            Pm[l] = p; Vn[l] = v; vgn[h.R + r] = v;
+            const T mq = MV[l] * q;
+            a[0] += q * p; a[1] += p * v; a[2] += p * qo; a[3] += mq * q; a[4] += mq * qo;
+          });
         });
       }
       if (!(ok = reduce(a))) break;
     }
     __syncthreads();
-    each_block([&](const Hdr& h, uint32_t l0) {
-      for (int r = lane; r < h.C; r += 32) xout[h.R + r] = X[l0 + r];
+    each_part([&](const Hdr& h, uint32_t l0, int j0, int nj) {
+      each_row(h, j0, nj, [&](int r) { xout[h.R + r] = X[l0 + r]; });
     });
     if (cta == 0 && threadIdx.x == 0) {
       if (!ok) { S.status = HS_TIMEOUT; S.done = 2; }
